@@ -1,0 +1,283 @@
+/*
+ * MinMaxLTTB oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of what the MinMaxLTTB method of
+ * "MinMaxLTTB: Leveraging MinMax-Preselection to Scale LTTB" (arXiv 2305.00332)
+ * computes.  Only the test suite, the package smoke check and the benchmark's CPU
+ * baseline load this file's shared library; the CUDA library never does, and the
+ * two share no code.  Build with  -O2 -ffp-contract=off  and no fast-math, so that
+ * every floating-point sum, difference and product below is rounded on its own,
+ * in the order written (GCC on aarch64 would otherwise contract a*b-c*d to FMA).
+ *
+ * What the paper states (Sec. 3):
+ *   - MinMaxLTTB is two steps: MinMax preselects vertical extrema (the argmin and
+ *     argmax of each bin), then LTTB runs on the preselected points only.
+ *   - The first and last point of the series are always handed to LTTB.
+ *   - r_ps * n_out points are preselected; r_ps/2 MinMax sub-buckets per LTTB
+ *     bucket, i.e. n_out * r_ps / 2 MinMax bins.
+ * What it takes from Sec. 2.2.1 and the LTTB thesis it cites:
+ *   - MinMax: per bin B_i, the vertical extrema via (arg)min and (arg)max.
+ *   - LTTB: per bucket B_i, the point forming the largest triangle with the
+ *     point selected in B_{i-1} and the average (mean x, mean y) of B_{i+1}.
+ *
+ * Readings where the paper is silent (numbered R1..R15 wherever they are cited):
+ *   R1  LTTB buckets: first and last point fixed, K = n_out-2 buckets over the
+ *       interior positions 1..m-2, bucket j = [floor(j(m-2)/K)+1, floor((j+1)(m-2)/K)+1)
+ *       in exact integer arithmetic.
+ *   R2  MinMax bins, index mode: B = floor(n_out*r_ps/2) bins over the interior
+ *       points 1..n-2, bin i = [floor(i(n-2)/B)+1, floor((i+1)(n-2)/B)+1).
+ *   R3  MinMax bins, x mode (int64 x, non-decreasing): edges
+ *       e_i = x_0 + floor(i (x_{n-1}-x_0) / B); interior point p is in the largest
+ *       bin i with e_i <= x_p (so the last bin runs up to and including x_{n-1}).
+ *       Empty bins emit nothing.
+ *   R4  LTTB over preselected points: buckets are formed over positions in the
+ *       preselected list; means and areas use the original coordinates.
+ *   R5  The next bucket of the last bucket is the single last point.
+ *   R6  Area = |(xa-xc)(yb-ya) - (xa-xb)(yc-ya)| in FP64, each product and
+ *       difference rounded separately, without the factor 1/2.  Implicit x is
+ *       the index as a double.
+ *   R7  Mean = FP64 sum from left to right over the bucket, then one division by
+ *       the count.
+ *   R8  Ties: the lowest index wins, in MinMax (min and max) and in LTTB.
+ *   R9  A bin whose argmin equals its argmax emits that index once.
+ *   R10 -0.0 and +0.0 compare equal (IEEE), so they tie.
+ *   R11 NaN in y is a precondition violation; the output is then unspecified.
+ *   R12 B = floor(n_out*r_ps/2) for odd products.
+ *   R13 minmaxlttb rejects r_ps < 2; minmax_preselect alone accepts r_ps >= 1.
+ *   R14 When fewer than n_out points are preselected (x mode), all are returned.
+ *   R15 When r_ps*n_out >= n, minmaxlttb is plain LTTB on all points; when
+ *       n_out >= n it returns every index.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MMO_EINVAL (-1)
+#define MMO_ENOMEM (-5)
+
+enum { Y_F32 = 0, Y_F64 = 1 };
+enum { X_IMPLICIT = 0, X_I64 = 1, X_F64 = 2 };
+enum { BINS_INDEX = 0, BINS_XWIDTH = 1 };
+
+/* The y value of point i as a double (a float converts exactly). */
+static double y_at(const void *y, int ydt, int64_t i)
+{
+    if (ydt == Y_F32) return (double)((const float *)y)[i];
+    return ((const double *)y)[i];
+}
+
+/* The x coordinate of point i as a double (R6: implicit x is the index). */
+static double x_at(const void *x, int xk, int64_t i)
+{
+    if (xk == X_IMPLICIT) return (double)i;
+    if (xk == X_I64) return (double)((const int64_t *)x)[i];
+    return ((const double *)x)[i];
+}
+
+/* floor(a*b/c) + 1 for 0 <= a <= c, b >= 0, c > 0: the start of part a when
+   b items are split into c equal-count parts (R1, R2). */
+static int64_t part_start(int64_t a, int64_t b, int64_t c)
+{
+    unsigned __int128 num = (unsigned __int128)(uint64_t)a * (uint64_t)b;
+    return (int64_t)(num / (uint64_t)c) + 1;
+}
+
+static int check_common(const void *y, int ydt, const void *x, int xk, int64_t n)
+{
+    if (n < 0) return MMO_EINVAL;
+    if (n > 0 && y == NULL) return MMO_EINVAL;
+    if (ydt != Y_F32 && ydt != Y_F64) return MMO_EINVAL;
+    if (xk != X_IMPLICIT && xk != X_I64 && xk != X_F64) return MMO_EINVAL;
+    if (xk != X_IMPLICIT && n > 0 && x == NULL) return MMO_EINVAL;
+    return 0;
+}
+
+/*
+ * MinMax per bin (Sec. 2.2.1; the preselection of Sec. 3).  For each of the B
+ * bins over the interior points 1..n-2, writes the index of the first minimum and
+ * of the first maximum of y, or -1 for both when the bin is empty.
+ * Bins follow R2 (index mode) or R3 (x mode).  Returns B, or a negative error.
+ */
+int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n,
+                        int64_t B, int binmode, int64_t *imin, int64_t *imax)
+{
+    int rc = check_common(y, ydt, x, xk, n);
+    if (rc) return rc;
+    if (B < 1) return MMO_EINVAL;
+    if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+
+    double *vmin = (double *)malloc(sizeof(double) * (size_t)B);
+    double *vmax = (double *)malloc(sizeof(double) * (size_t)B);
+    if (!vmin || !vmax) { free(vmin); free(vmax); return MMO_ENOMEM; }
+    for (int64_t b = 0; b < B; b++) { imin[b] = -1; imax[b] = -1; }
+
+    const int64_t N = n - 2; /* interior points 1..n-2 */
+    const int64_t *xi = (const int64_t *)x;
+    int64_t x0 = 0, D = 0;
+    if (binmode == BINS_XWIDTH && n >= 2) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
+
+    int64_t b = 0;
+    for (int64_t p = 1; p <= n - 2; p++) {
+        /* Move to the last bin whose start is at or before p. */
+        for (;;) {
+            if (b + 1 >= B) break;
+            int starts_by_p;
+            if (binmode == BINS_INDEX) {
+                starts_by_p = part_start(b + 1, N, B) <= p;
+            } else {
+                /* e_{b+1} = x_0 + floor((b+1) D / B) <= x_p  (R3) */
+                __int128 q = ((__int128)(b + 1) * (__int128)D) / (__int128)B;
+                starts_by_p = (__int128)x0 + q <= (__int128)xi[p];
+            }
+            if (!starts_by_p) break;
+            b++;
+        }
+        double v = y_at(y, ydt, p);
+        if (imin[b] < 0) {
+            imin[b] = p; imax[b] = p; vmin[b] = v; vmax[b] = v;
+        } else {
+            /* strict comparisons keep the first occurrence (R8, R10) */
+            if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }
+            if (v > vmax[b]) { vmax[b] = v; imax[b] = p; }
+        }
+    }
+    free(vmin);
+    free(vmax);
+    return B;
+}
+
+/*
+ * MinMax preselection (Sec. 3, first step): point 0, then for each non-empty bin
+ * its argmin and argmax in increasing index order (once if equal, R9), then point
+ * n-1.  B = floor(n_out*r_ps/2) (R12).  out must hold 2B+2 indices.
+ * Returns the number of indices written, or a negative error.
+ */
+int64_t mmo_minmax_preselect(const void *y, int ydt, const void *x, int xk, int64_t n,
+                             int64_t n_out, int32_t r_ps, int binmode, int64_t *out)
+{
+    int rc = check_common(y, ydt, x, xk, n);
+    if (rc) return rc;
+    if (n_out < 1 || r_ps < 1) return MMO_EINVAL;
+    if (n_out > INT64_MAX / r_ps) return MMO_EINVAL;
+    int64_t B = n_out * (int64_t)r_ps / 2;
+    if (B < 1) return MMO_EINVAL;
+    if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    if (n == 0) return 0;
+    if (n == 1) { out[0] = 0; return 1; }
+
+    int64_t *imin = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    int64_t *imax = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    if (!imin || !imax) { free(imin); free(imax); return MMO_ENOMEM; }
+    int64_t r = mmo_minmax_bins(y, ydt, x, xk, n, B, binmode, imin, imax);
+    if (r < 0) { free(imin); free(imax); return r; }
+
+    int64_t m = 0;
+    out[m++] = 0;
+    for (int64_t b = 0; b < B; b++) {
+        if (imin[b] < 0) continue; /* empty bin (R3) */
+        int64_t lo = imin[b] < imax[b] ? imin[b] : imax[b];
+        int64_t hi = imin[b] < imax[b] ? imax[b] : imin[b];
+        out[m++] = lo;
+        if (hi != lo) out[m++] = hi;
+    }
+    out[m++] = n - 1;
+    free(imin);
+    free(imax);
+    return m;
+}
+
+/*
+ * LTTB (Sec. 2.2.1 and the thesis it cites) on the m points at positions 0..m-1,
+ * where position p is original point idx[p] (idx == NULL: position p is point p).
+ * Buckets R1, next-bucket mean R5/R7, area R6, ties R8.  Writes min(n_out, m)
+ * original indices to out and returns that count, or a negative error.
+ */
+int64_t mmo_lttb_positions(const void *y, int ydt, const void *x, int xk,
+                           const int64_t *idx, int64_t m, int64_t n_out, int64_t *out)
+{
+    int rc = check_common(y, ydt, x, xk, m);
+    if (rc) return rc;
+    if (n_out < 0) return MMO_EINVAL;
+#define IDX(p) (idx ? idx[(p)] : (int64_t)(p))
+    if (n_out >= m) { /* nothing to drop: every point (R14, R15) */
+        for (int64_t p = 0; p < m; p++) out[p] = IDX(p);
+        return m;
+    }
+    if (n_out < 3) return MMO_EINVAL;
+
+    const int64_t K = n_out - 2; /* buckets */
+    const int64_t N = m - 2;     /* interior positions, N > K */
+    int64_t a = 0;               /* position of the previously selected point */
+    out[0] = IDX(0);
+    for (int64_t j = 0; j < K; j++) {
+        int64_t lo = part_start(j, N, K);
+        int64_t hi = part_start(j + 1, N, K);
+        int64_t nlo, nhi;
+        if (j + 1 < K) { nlo = hi; nhi = part_start(j + 2, N, K); }
+        else { nlo = m - 1; nhi = m; } /* R5 */
+
+        /* mean of the next bucket: left-to-right sums, one division (R7) */
+        double sx = 0.0, sy = 0.0;
+        for (int64_t p = nlo; p < nhi; p++) {
+            sx = sx + x_at(x, xk, IDX(p));
+            sy = sy + y_at(y, ydt, IDX(p));
+        }
+        double cnt = (double)(nhi - nlo);
+        double xc = sx / cnt, yc = sy / cnt;
+
+        double xa = x_at(x, xk, IDX(a)), ya = y_at(y, ydt, IDX(a));
+        double best = -1.0;
+        int64_t pick = lo;
+        for (int64_t p = lo; p < hi; p++) {
+            double xb = x_at(x, xk, IDX(p)), yb = y_at(y, ydt, IDX(p));
+            double area = fabs((xa - xc) * (yb - ya) - (xa - xb) * (yc - ya));
+            if (p == lo || area > best) { best = area; pick = p; } /* R8 */
+        }
+        out[j + 1] = IDX(pick);
+        a = pick;
+    }
+    out[K + 1] = IDX(m - 1);
+#undef IDX
+    return n_out;
+}
+
+/* Plain LTTB on all n points. */
+int64_t mmo_lttb(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t n_out,
+                 int64_t *out)
+{
+    return mmo_lttb_positions(y, ydt, x, xk, NULL, n, n_out, out);
+}
+
+/*
+ * MinMaxLTTB (Sec. 3): n_out >= n returns every index; r_ps*n_out >= n runs LTTB
+ * on all points (R15); otherwise MinMax preselection followed by LTTB on the
+ * preselected points (R4, R14).  out holds min(n_out, n) indices.
+ */
+int64_t mmo_minmaxlttb(const void *y, int ydt, const void *x, int xk, int64_t n,
+                       int64_t n_out, int32_t r_ps, int binmode, int64_t *out)
+{
+    int rc = check_common(y, ydt, x, xk, n);
+    if (rc) return rc;
+    if (n_out < 0) return MMO_EINVAL;
+    if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    if (n_out >= n) {
+        for (int64_t p = 0; p < n; p++) out[p] = p;
+        return n;
+    }
+    if (n_out < 3 || r_ps < 2) return MMO_EINVAL;
+    if (n_out > INT64_MAX / r_ps) return MMO_EINVAL;
+    if ((int64_t)r_ps * n_out >= n) return mmo_lttb(y, ydt, x, xk, n, n_out, out);
+
+    int64_t B = n_out * (int64_t)r_ps / 2;
+    int64_t *sel = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * B + 2));
+    if (!sel) return MMO_ENOMEM;
+    int64_t m = mmo_minmax_preselect(y, ydt, x, xk, n, n_out, r_ps, binmode, sel);
+    if (m < 0) { free(sel); return m; }
+    int64_t r = mmo_lttb_positions(y, ydt, x, xk, sel, m, n_out, out);
+    free(sel);
+    return r;
+}

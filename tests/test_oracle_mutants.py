@@ -1,0 +1,85 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that at
+least one pin catches each: the pins are strong enough to trust the oracle."""
+import json
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+import pins
+from oracle import CFLAGS, SRC, Oracle
+
+# (name, original text, mutated text); each original must occur exactly once.
+MUTANTS = [
+    ("area_sign_first_term", "(xa - xc) * (yb - ya)", "(xa - xc) * (ya - yb)"),
+    ("area_wrong_point", "(xa - xb) * (yc - ya)", "(xa - xb) * (yc - yb)"),
+    ("area_transposed_operand", "(xa - xb) * (yc - ya)", "(xb - xa) * (yc - ya)"),
+    ("area_dropped_term", "fabs((xa - xc) * (yb - ya) - (xa - xb) * (yc - ya))", "fabs((xa - xc) * (yb - ya))"),
+    ("mean_count_off_by_one", "double cnt = (double)(nhi - nlo);", "double cnt = (double)(nhi - nlo + 1);"),
+    ("mean_uses_x_for_y", "sy = sy + y_at(y, ydt, IDX(p));", "sy = sy + x_at(x, xk, IDX(p));"),
+    ("next_bucket_is_current", "if (j + 1 < K) { nlo = hi; nhi = part_start(j + 2, N, K); }",
+     "if (j + 1 < K) { nlo = lo; nhi = hi; }"),
+    ("lttb_tie_last_wins", "if (p == lo || area > best)", "if (p == lo || area >= best)"),
+    ("previous_pick_not_advanced", "        a = pick;\n", "\n"),
+    ("bucket_start_ceil", "return (int64_t)(num / (uint64_t)c) + 1;",
+     "return (int64_t)((num + (uint64_t)c - 1) / (uint64_t)c) + 1;"),
+    ("minmax_tie_last_min", "if (v < vmin[b])", "if (v <= vmin[b])"),
+    ("minmax_tie_last_max", "if (v > vmax[b])", "if (v >= vmax[b])"),
+    ("minmax_includes_first_point", "for (int64_t p = 1; p <= n - 2; p++) {", "for (int64_t p = 0; p <= n - 2; p++) {"),
+    ("minmax_includes_last_point", "for (int64_t p = 1; p <= n - 2; p++) {", "for (int64_t p = 1; p <= n - 1; p++) {"),
+    ("last_point_dropped", "    out[m++] = n - 1;\n", "\n"),
+    ("no_dedupe_equal_extrema", "if (hi != lo) out[m++] = hi;", "out[m++] = hi;"),
+    ("xwidth_edge_strict", "(__int128)x0 + q <= (__int128)xi[p]", "(__int128)x0 + q < (__int128)xi[p]"),
+    ("bins_from_r_ps_not_halved", "int64_t B = n_out * (int64_t)r_ps / 2;\n    if (B < 1) return MMO_EINVAL;",
+     "int64_t B = n_out * (int64_t)r_ps;\n    if (B < 1) return MMO_EINVAL;"),
+    ("no_lttb_when_rps_covers_n", "if ((int64_t)r_ps * n_out >= n) return mmo_lttb(y, ydt, x, xk, n, n_out, out);", ""),
+]
+
+
+def _build_mutant(tmpdir, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutant {name}: anchor text found {src.count(old)} times"
+    path_c = os.path.join(tmpdir, f"{name}.c")
+    path_so = os.path.join(tmpdir, f"lib{name}.so")
+    with open(path_c, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", *CFLAGS, path_c, "-o", path_so, "-lm"], check=True)
+    return path_so
+
+
+@pytest.fixture(scope="module")
+def tmpdir():
+    with tempfile.TemporaryDirectory() as d:
+        yield d
+
+
+_CHILD = r"""
+import json, sys
+sys.path[:0] = [sys.argv[2], sys.argv[3]]
+import pins
+from oracle import Oracle
+o = Oracle(sys.argv[1])
+caught = []
+for check in pins.ALL_CHECKS:
+    try:
+        check(o)
+    except Exception as e:
+        caught.append(check.__name__)
+print(json.dumps(caught))
+"""
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmpdir, name, old, new):
+    so = _build_mutant(tmpdir, name, old, new)
+    here = os.path.dirname(os.path.abspath(__file__))
+    # A child process: a mutant that writes out of bounds may crash, which also
+    # counts as detected.
+    r = subprocess.run([sys.executable, "-c", _CHILD, so, here, os.path.dirname(here)],
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return
+    caught = json.loads(r.stdout.strip().splitlines()[-1])
+    assert caught, f"no pin detects the planted mistake {name}"
