@@ -1,0 +1,175 @@
+/*
+ * mmlttb.h -- C ABI of the GB300 (sm_103a) MinMaxLTTB library, libmmlttb.so.
+ *
+ * MinMaxLTTB (arXiv 2305.00332, Sec. 3) downsamples a time series of n_in points
+ * to n_out indices in two steps: MinMax preselection keeps the argmin and argmax
+ * of y in each of floor(n_out*r_ps/2) bins (plus the first and last point), then
+ * LTTB (Sec. 2.2.1) picks one point per bucket among the preselected points.
+ * Every result is a selection, returned as strictly increasing int64 indices into
+ * the input series.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named y, x, out_idx, out_count and workspace are DEVICE pointers
+ *     (or host memory the device can address); the caller allocates and owns them.
+ *     Nothing is allocated or freed by these calls.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) unless stated otherwise.  Results are valid once the stream has
+ *     reached the call.  Calls that overlap on the GPU must not share a workspace.
+ *   - The return value is MMLTTB_OK (0) or a negative MMLTTB_E* code; argument
+ *     errors are detected on the host before anything is enqueued.  No C++
+ *     exception crosses this interface.
+ *   - y is float32 or float64, contiguous.  x is implicit (the index 0..n_in-1),
+ *     int64 or float64, contiguous, and non-decreasing (a precondition that is not
+ *     checked).  y must contain no NaN (precondition, not checked).
+ *   - Ties go to the lowest index; -0.0 and +0.0 are equal.  The LTTB areas and
+ *     bucket means are computed in FP64 exactly as
+ *       area = |(xa-xc)*(yb-ya) - (xa-xb)*(yc-ya)|   (each operation rounded on its own)
+ *       mean = (((v0 + v1) + v2) + ...) / count       (left to right)
+ *     so results are bit-identical to a sequential CPU statement of the method.
+ */
+#ifndef MMLTTB_H
+#define MMLTTB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define MMLTTB_OK 0
+#define MMLTTB_EINVAL (-1)   /* invalid argument (null pointer, size, enum, r_ps, n_out) */
+#define MMLTTB_ENOSPC (-2)   /* workspace smaller than the size query returned */
+#define MMLTTB_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define MMLTTB_ETIMEOUT (-4) /* a bounded device-side wait gave up (status word) */
+#define MMLTTB_ERANGE (-6)   /* output capacity too small */
+#define MMLTTB_EDEVICE (-7)  /* a device-side check failed (status word) */
+
+/* Element type of y. */
+#define MMLTTB_F32 0
+#define MMLTTB_F64 1
+
+/* Kind of x. */
+#define MMLTTB_X_IMPLICIT 0 /* x = index; the x pointer is ignored (may be NULL) */
+#define MMLTTB_X_I64 1      /* int64, non-decreasing */
+#define MMLTTB_X_F64 2      /* float64, non-decreasing (index bins only) */
+
+/* How MinMax bins partition the interior points 1..n_in-2. */
+#define MMLTTB_BINS_INDEX 0  /* equal count: bin i = [floor(i(n-2)/B)+1, floor((i+1)(n-2)/B)+1) */
+#define MMLTTB_BINS_XWIDTH 1 /* equal x width (int64 x only): edges e_i = x0 + floor(i(x_{n-1}-x0)/B);
+                                point p is in the largest bin i with e_i <= x_p; empty bins emit nothing */
+
+/* Operation selector for mmlttb_workspace_bytes. */
+#define MMLTTB_OP_PRESELECT 0
+#define MMLTTB_OP_LTTB 1
+#define MMLTTB_OP_MINMAXLTTB 2
+
+/* Opaque CUDA stream handle; binary-compatible with cudaStream_t. */
+typedef struct CUstream_st *mmlttb_stream;
+
+/* Human-readable text for a return code; never NULL, static storage. */
+const char *mmlttb_strerror(int code);
+
+/* The cudaError_t value of the most recent MMLTTB_ECUDA on the calling thread. */
+int mmlttb_last_cuda_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int mmlttb_version(void);
+
+/*
+ * Workspace size (bytes, on the current device) needed by `op` for these sizes.
+ * Writes the size to *bytes.  The size depends only on the arguments and on the
+ * current device's SM count.  Returns MMLTTB_OK or MMLTTB_EINVAL.
+ */
+int mmlttb_workspace_bytes(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out,
+                           int32_t r_ps, int binmode, size_t *bytes);
+
+/*
+ * MinMax preselection (Sec. 3, first step; MinMax of Sec. 2.2.1 and Table 1).
+ * B = floor(n_out*r_ps/2) bins (r_ps >= 1, B >= 1) over the interior points
+ * 1..n_in-2.  Writes point 0, then per non-empty bin its argmin and argmax of y in
+ * increasing index order (once when they coincide), then point n_in-1: at most
+ * 2B+2 strictly increasing indices.
+ *   out_idx   device int64[out_cap]; out_cap must be >= min(n_in, 2B+2), else MMLTTB_ERANGE.
+ *   out_count device int64 (nullable): receives the number of indices written.
+ *   workspace device memory of at least mmlttb_workspace_bytes(MMLTTB_OP_PRESELECT, ...) bytes.
+ */
+int mmlttb_minmax_preselect(const void *y, int ydtype, const void *x, int xkind, int64_t n_in,
+                            int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
+                            int64_t out_cap, int64_t *out_count, void *workspace,
+                            size_t workspace_bytes, mmlttb_stream stream);
+
+/*
+ * LTTB (Largest-Triangle-Three-Buckets; Sec. 2.2.1 and Table 1 of the paper, after
+ * Steinarsson's thesis) on all n_in points.  n_out >= n_in returns 0..n_in-1;
+ * otherwise n_out >= 3 is required: first and last point are kept and each of the
+ * n_out-2 buckets [floor(j(n-2)/K)+1, floor((j+1)(n-2)/K)+1) contributes the point
+ * with the largest triangle area against the previous pick and the mean of the next
+ * bucket (the last bucket's next bucket is the last point).
+ *   out_idx   device int64[out_cap], out_cap >= min(n_out, n_in).
+ *   out_count device int64 (nullable): receives min(n_out, n_in).
+ */
+int mmlttb_lttb(const void *y, int ydtype, const void *x, int xkind, int64_t n_in,
+                int64_t n_out, int64_t *out_idx, int64_t out_cap, int64_t *out_count,
+                void *workspace, size_t workspace_bytes, mmlttb_stream stream);
+
+/*
+ * MinMaxLTTB (Sec. 3): n_out >= n_in returns every index; n_out < 3 or r_ps < 2 is
+ * MMLTTB_EINVAL; r_ps*n_out >= n_in runs LTTB on all points; otherwise MinMax
+ * preselection (as mmlttb_minmax_preselect) followed by LTTB on the preselected
+ * points, buckets formed over positions in the preselected list and areas/means
+ * taken from the original x and y.  When fewer than n_out points are preselected
+ * (possible with x-width bins) all of them are returned.
+ *   out_idx   device int64[out_cap], out_cap >= min(n_out, n_in).
+ *   out_count device int64 (nullable): number of indices written (min(n_out, n_in)
+ *             with index bins).
+ */
+int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64_t n_in,
+                      int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
+                      int64_t out_cap, int64_t *out_count, void *workspace,
+                      size_t workspace_bytes, mmlttb_stream stream);
+
+/*
+ * MinMaxLTTB on HOST buffers, end to end (blocking).  Copies y (and x) from host
+ * memory into `device_buffer` (pinned host memory makes the copies asynchronous
+ * DMA), runs mmlttb_minmaxlttb there, copies the indices and the count back to
+ * out_host / out_count_host, and synchronizes `stream` before returning.
+ *   device_buffer  device memory of at least mmlttb_host_buffer_bytes(...) bytes,
+ *                  owned by the caller (holds the staged input, the output and the
+ *                  workspace).
+ *   out_host       host int64[out_cap], out_cap >= min(n_out, n_in).
+ *   out_count_host host int64 (nullable).
+ */
+int mmlttb_host_buffer_bytes(int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                             int binmode, size_t *bytes);
+int mmlttb_minmaxlttb_host(const void *y_host, int ydtype, const void *x_host, int xkind,
+                           int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
+                           int64_t *out_host, int64_t out_cap, int64_t *out_count_host,
+                           void *device_buffer, size_t device_bytes, mmlttb_stream stream);
+
+/*
+ * Profiling hook (per calling thread, one shot): the next call that runs MinMax
+ * preselection records `start_event` on its stream just before the streaming
+ * MinMax kernel and `stop_event` just after it, then forgets both.  The events
+ * are cudaEvent_t handles created by the caller (NULL, NULL disarms).  The time
+ * between them is that kernel's device time.
+ */
+int mmlttb_set_timing_events(void *start_event, void *stop_event);
+
+/* Number of kernels this library has launched from the calling thread so far. */
+unsigned long long mmlttb_launch_count(void);
+
+/*
+ * Read the workspace's status word (blocking: synchronizes `stream`).  *status
+ * receives 0 when no device-side wait timed out and no device check failed since
+ * the workspace was last cleared; otherwise a bitmask (1 = a bounded wait timed
+ * out, 2 = a device check failed).  Returns MMLTTB_OK, or MMLTTB_ECUDA.
+ */
+int mmlttb_workspace_status(const void *workspace, int *status, mmlttb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMLTTB_H */

@@ -118,21 +118,21 @@ int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n
     int64_t x0 = 0, D = 0;
     if (binmode == BINS_XWIDTH && n >= 2) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
 
+    /* start (index mode) or left edge (x mode) of bin b+1; past the last bin, a bound
+       above every int64 */
+#define NEXT_BOUND(bb)                                                                  \
+    ((bb) + 1 >= B ? (__int128)INT64_MAX + 1                                            \
+     : binmode == BINS_INDEX ? (__int128)part_start((bb) + 1, N, B)                     \
+     : (__int128)x0 + ((__int128)((bb) + 1) * (__int128)D) / (__int128)B)
     int64_t b = 0;
+    __int128 next = NEXT_BOUND(b);
     for (int64_t p = 1; p <= n - 2; p++) {
-        /* Move to the last bin whose start is at or before p. */
-        for (;;) {
-            if (b + 1 >= B) break;
-            int starts_by_p;
-            if (binmode == BINS_INDEX) {
-                starts_by_p = part_start(b + 1, N, B) <= p;
-            } else {
-                /* e_{b+1} = x_0 + floor((b+1) D / B) <= x_p  (R3) */
-                __int128 q = ((__int128)(b + 1) * (__int128)D) / (__int128)B;
-                starts_by_p = (__int128)x0 + q <= (__int128)xi[p];
-            }
-            if (!starts_by_p) break;
+        /* Move to the last bin whose start is at or before p:
+           index mode: start(b+1) <= p;  x mode: e_{b+1} = x_0 + floor((b+1) D / B) <= x_p (R3) */
+        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
+        while (next <= here) {
             b++;
+            next = NEXT_BOUND(b);
         }
         double v = y_at(y, ydt, p);
         if (imin[b] < 0) {
@@ -143,6 +143,7 @@ int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n
             if (v > vmax[b]) { vmax[b] = v; imax[b] = p; }
         }
     }
+#undef NEXT_BOUND
     free(vmin);
     free(vmax);
     return B;

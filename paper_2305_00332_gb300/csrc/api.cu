@@ -1,0 +1,421 @@
+// C ABI of libmmlttb: argument checks, planning, workspace layout and the launch
+// sequence of the MinMaxLTTB hot path (arXiv 2305.00332, Sec. 3).
+//
+// Launch sequence for one series (all on the caller's stream, no host sync):
+//   memset(header) -> [k_edges] -> k_stream -> k_merge -> k_tables -> k_chain
+// (or k_lttb_grid instead of the table pair when LTTB buckets are large), or
+// k_iota when every index is kept.
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+using namespace mmlttb;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+thread_local unsigned long long g_launches = 0;   // kernels launched by this thread
+thread_local cudaEvent_t g_ev_start = nullptr;     // one-shot events around k_stream
+thread_local cudaEvent_t g_ev_stop = nullptr;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return MMLTTB_ECUDA;
+}
+
+struct DevInfo {
+  int sms = 0;
+  int stream_bps = 0;
+  int grid_bps = 0;
+  bool ok = false;
+};
+
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+
+int get_dev_info(DevInfo* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev >= 0 && dev < 64 && g_dev[dev].ok) {
+    *out = g_dev[dev];
+    return MMLTTB_OK;
+  }
+  DevInfo d;
+  e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  d.stream_bps = stream_blocks_per_sm();
+  d.grid_bps = lttb_grid_blocks_per_sm();
+  d.ok = true;
+  if (dev >= 0 && dev < 64) g_dev[dev] = d;
+  *out = d;
+  return MMLTTB_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr size_t kHeader = 256;  // status word @0, barrier counter @4, m @8
+
+struct SinglePlan {
+  int32_t branch = BR_ARANGE, engine = EN_NONE;
+  int64_t B = 0, K = 0, npos = 0, W = 0, Wcap = 0, tab_cap = 0;
+  int grid_lttb = 0;
+  size_t off_edges = 0, off_rec = 0, off_sel = 0, off_tab = 0, off_means = 0, off_partial = 0;
+  size_t total = kHeader;
+};
+
+// Largest LTTB bucket over m positions with K buckets: ceil((m-2)/K).
+int64_t max_bucket(int64_t m, int64_t K) { return (m - 2 + K - 1) / K; }
+
+// Host-only validation and branch choice (Sec. 3 dispatch); needs no device.
+int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
+             int32_t* branch, int64_t* bins) {
+  if (ydt != MMLTTB_F32 && ydt != MMLTTB_F64) return MMLTTB_EINVAL;
+  if (xk != MMLTTB_X_IMPLICIT && xk != MMLTTB_X_I64 && xk != MMLTTB_X_F64) return MMLTTB_EINVAL;
+  if (n < 0 || n_out < 0) return MMLTTB_EINVAL;
+  const bool uses_bins = op == MMLTTB_OP_PRESELECT || op == MMLTTB_OP_MINMAXLTTB;
+  if (uses_bins) {
+    if (binmode != MMLTTB_BINS_INDEX && binmode != MMLTTB_BINS_XWIDTH) return MMLTTB_EINVAL;
+    if (binmode == MMLTTB_BINS_XWIDTH && xk != MMLTTB_X_I64) return MMLTTB_EINVAL;
+  }
+  int64_t B = 0;
+  int32_t br;
+  switch (op) {
+    case MMLTTB_OP_PRESELECT:
+      if (n_out < 1 || r_ps < 1) return MMLTTB_EINVAL;
+      if (n_out > INT64_MAX / r_ps) return MMLTTB_EINVAL;
+      B = n_out * (int64_t)r_ps / 2;
+      if (B < 1) return MMLTTB_EINVAL;
+      br = BR_PRESELECT;
+      break;
+    case MMLTTB_OP_LTTB:
+      if (n_out >= n) br = BR_ARANGE;
+      else if (n_out < 3) return MMLTTB_EINVAL;
+      else br = BR_LTTB_ALL;
+      break;
+    case MMLTTB_OP_MINMAXLTTB:
+      if (n_out >= n) { br = BR_ARANGE; break; }
+      if (n_out < 3 || r_ps < 2) return MMLTTB_EINVAL;
+      if (n_out > INT64_MAX / r_ps) return MMLTTB_EINVAL;
+      if ((int64_t)r_ps * n_out >= n) { br = BR_LTTB_ALL; break; }
+      B = n_out * (int64_t)r_ps / 2;
+      br = BR_MINMAX_LTTB;
+      break;
+    default:
+      return MMLTTB_EINVAL;
+  }
+  if (B >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // bins are indexed with int on device
+  *branch = br;
+  *bins = B;
+  return MMLTTB_OK;
+}
+
+int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
+                const DevInfo& d, SinglePlan* P) {
+  SinglePlan p;
+  int rc = classify(op, ydt, xk, n, n_out, r_ps, binmode, &p.branch, &p.B);
+  if (rc) return rc;
+  size_t off = kHeader;
+  if (p.branch == BR_PRESELECT || p.branch == BR_MINMAX_LTTB) {
+    p.npos = n > 2 ? n - 2 : 0;
+    p.Wcap = (int64_t)d.sms * d.stream_bps * kStreamWarps;
+    p.W = p.npos < p.Wcap ? p.npos : p.Wcap;
+    if (p.W > 0 && p.npos / p.W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // per-warp span
+    if (binmode == MMLTTB_BINS_XWIDTH) {
+      p.off_edges = off;
+      off = align256(off + (size_t)(p.B + 1) * 8);
+    }
+    p.off_rec = off;
+    off = align256(off + (size_t)(p.B + p.Wcap) * sizeof(Record));
+  }
+  if (p.branch == BR_MINMAX_LTTB) {
+    p.off_sel = off;
+    off = align256(off + (size_t)(2 * p.B + 2) * 8);
+  }
+  if (p.branch == BR_LTTB_ALL || p.branch == BR_MINMAX_LTTB) {
+    p.K = n_out - 2;
+    const int64_t mcap = p.branch == BR_LTTB_ALL ? n : 2 * p.B + 2;
+    p.engine = max_bucket(mcap, p.K) <= kTableMaxBucket ? EN_TABLES : EN_GRID;
+    if (p.engine == EN_TABLES) {
+      p.tab_cap = mcap;
+      p.off_tab = off;
+      off = align256(off + (size_t)mcap);
+    } else {
+      p.grid_lttb = d.sms * d.grid_bps;
+      p.off_means = off;
+      off = align256(off + (size_t)p.K * 16);
+      p.off_partial = off;
+      off = align256(off + (size_t)p.grid_lttb * 32);
+    }
+  }
+  p.total = off;
+  *P = p;
+  return MMLTTB_OK;
+}
+
+int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n, int64_t n_out,
+               int32_t r_ps, int binmode, int64_t* out, int64_t out_cap, int64_t* out_count,
+               void* ws, size_t ws_bytes, cudaStream_t st) {
+  int32_t branch;
+  int64_t bins;
+  int rc = classify(op, ydt, xk, n, n_out, r_ps, binmode, &branch, &bins);
+  if (rc) return rc;
+  if (n > 0 && y == nullptr) return MMLTTB_EINVAL;
+  if (xk != MMLTTB_X_IMPLICIT && n > 0 && x == nullptr) return MMLTTB_EINVAL;
+  const int64_t need = branch == BR_PRESELECT ? (n < 2 * bins + 2 ? n : 2 * bins + 2)
+                                              : (n_out < n ? n_out : n);
+  if (need > 0 && out == nullptr) return MMLTTB_EINVAL;
+  if (out_cap < need) return MMLTTB_ERANGE;
+  DevInfo d;
+  rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(op, ydt, xk, n, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  if (ws == nullptr || ws_bytes < p.total) return MMLTTB_ENOSPC;
+
+  char* w = (char*)ws;
+  Batch bt;
+  memset(&bt, 0, sizeof(bt));
+  bt.plans = nullptr;
+  bt.n_series = 1;
+  bt.status = (unsigned*)w;
+  bt.barrier = (unsigned*)(w + 4);
+  SeriesPlan& sp = bt.one;
+  sp.y = y;
+  sp.x = xk == MMLTTB_X_IMPLICIT ? nullptr : x;
+  sp.ydt = ydt;
+  sp.xk = xk;
+  sp.binmode = binmode;
+  sp.branch = p.branch;
+  sp.engine = p.engine;
+  sp.r_ps = r_ps;
+  sp.n = n;
+  sp.n_out = n_out;
+  sp.B = p.B;
+  sp.bin_off = 0;
+  sp.edge_off = 0;
+  sp.pos_off = 0;
+  sp.npos = p.npos;
+  sp.tab_off = 0;
+  sp.tab_cap = p.tab_cap;
+  sp.m_ptr = (int64_t*)(w + 8);
+  sp.sel = p.branch == BR_PRESELECT ? out : (p.branch == BR_MINMAX_LTTB ? (int64_t*)(w + p.off_sel) : nullptr);
+  sp.tab = p.engine == EN_TABLES ? (uint8_t*)(w + p.off_tab) : nullptr;
+  sp.means = p.engine == EN_GRID ? (double*)(w + p.off_means) : nullptr;
+  sp.out = out;
+  sp.out_count = out_count;
+  bt.total_pos = p.npos;
+  bt.n_warps = p.W;
+  bt.total_edges = (p.B > 0 && binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
+  bt.total_slots = p.tab_cap;
+  bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
+  bt.edges = p.off_edges ? (int64_t*)(w + p.off_edges) : nullptr;
+  bt.partial = p.off_partial ? (double*)(w + p.off_partial) : nullptr;
+
+  cudaError_t e = cudaMemsetAsync(ws, 0, kHeader, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (p.branch == BR_ARANGE) {
+    e = launch_iota(out, n, out_count, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ++g_launches;
+    return MMLTTB_OK;
+  }
+  if (p.branch == BR_PRESELECT || p.branch == BR_MINMAX_LTTB) {
+    if (bt.total_edges > 0) {
+      if ((e = launch_edges(bt, st)) != cudaSuccess) return cuda_fail(e);
+      ++g_launches;
+    }
+    if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
+    if (p.W > 0) {
+      const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
+      if ((e = launch_stream(bt, grid, st)) != cudaSuccess) return cuda_fail(e);
+      ++g_launches;
+    }
+    if (g_ev_stop && (e = cudaEventRecord(g_ev_stop, st)) != cudaSuccess) return cuda_fail(e);
+    g_ev_start = g_ev_stop = nullptr;
+    if ((e = launch_merge(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
+    ++g_launches;
+  }
+  if (p.branch == BR_PRESELECT) return MMLTTB_OK;
+  if (p.engine == EN_TABLES) {
+    if ((e = launch_tables(bt, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_chain(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
+    g_launches += 2;
+  } else {
+    if (p.branch == BR_MINMAX_LTTB) {
+      if ((e = launch_chain(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
+      ++g_launches;
+    }
+    if ((e = launch_lttb_grid(bt, p.grid_lttb, st)) != cudaSuccess) return cuda_fail(e);
+    ++g_launches;
+  }
+  return MMLTTB_OK;
+}
+
+// Device staging layout of mmlttb_minmaxlttb_host: y | x | out | count | workspace.
+struct HostLayout {
+  size_t y = 0, x = 0, out = 0, count = 0, ws = 0, ws_bytes = 0, total = 0;
+};
+
+int host_layout(int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
+                HostLayout* L) {
+  int32_t branch;
+  int64_t bins;
+  int rc = classify(MMLTTB_OP_MINMAXLTTB, ydt, xk, n, n_out, r_ps, binmode, &branch, &bins);
+  if (rc) return rc;
+  DevInfo d;
+  rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(MMLTTB_OP_MINMAXLTTB, ydt, xk, n, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  const size_t es = ydt == MMLTTB_F32 ? 4 : 8;
+  const int64_t cap = n_out < n ? n_out : n;
+  HostLayout l;
+  size_t off = 0;
+  l.y = off;
+  off = align256(off + (size_t)n * es);
+  l.x = off;
+  off = align256(off + (xk == MMLTTB_X_IMPLICIT ? 0 : (size_t)n * 8));
+  l.out = off;
+  off = align256(off + (size_t)(cap > 0 ? cap : 1) * 8);
+  l.count = off;
+  off = align256(off + 8);
+  l.ws = off;
+  l.ws_bytes = p.total;
+  off = align256(off + p.total);
+  l.total = off;
+  *L = l;
+  return MMLTTB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mmlttb_strerror(int code) {
+  switch (code) {
+    case MMLTTB_OK: return "success";
+    case MMLTTB_EINVAL: return "invalid argument";
+    case MMLTTB_ENOSPC: return "workspace too small";
+    case MMLTTB_ECUDA: return "CUDA error";
+    case MMLTTB_ETIMEOUT: return "device-side wait timed out";
+    case MMLTTB_ERANGE: return "output capacity too small";
+    case MMLTTB_EDEVICE: return "device-side check failed";
+    default: return "unknown error";
+  }
+}
+
+int mmlttb_last_cuda_error(void) { return g_last_cuda_error; }
+
+int mmlttb_version(void) { return 100; }
+
+int mmlttb_workspace_bytes(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                           int binmode, size_t* bytes) {
+  if (!bytes) return MMLTTB_EINVAL;
+  int32_t branch;
+  int64_t bins;
+  int rc = classify(op, ydtype, xkind, n_in, n_out, r_ps, binmode, &branch, &bins);
+  if (rc) return rc;
+  DevInfo d;
+  rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(op, ydtype, xkind, n_in, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  *bytes = p.total;
+  return MMLTTB_OK;
+}
+
+int mmlttb_minmax_preselect(const void* y, int ydtype, const void* x, int xkind, int64_t n_in,
+                            int64_t n_out, int32_t r_ps, int binmode, int64_t* out_idx,
+                            int64_t out_cap, int64_t* out_count, void* workspace,
+                            size_t workspace_bytes, mmlttb_stream stream) {
+  return run_single(MMLTTB_OP_PRESELECT, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx,
+                    out_cap, out_count, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int mmlttb_lttb(const void* y, int ydtype, const void* x, int xkind, int64_t n_in, int64_t n_out,
+                int64_t* out_idx, int64_t out_cap, int64_t* out_count, void* workspace,
+                size_t workspace_bytes, mmlttb_stream stream) {
+  return run_single(MMLTTB_OP_LTTB, y, ydtype, x, xkind, n_in, n_out, 2, MMLTTB_BINS_INDEX, out_idx,
+                    out_cap, out_count, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int mmlttb_minmaxlttb(const void* y, int ydtype, const void* x, int xkind, int64_t n_in,
+                      int64_t n_out, int32_t r_ps, int binmode, int64_t* out_idx, int64_t out_cap,
+                      int64_t* out_count, void* workspace, size_t workspace_bytes,
+                      mmlttb_stream stream) {
+  return run_single(MMLTTB_OP_MINMAXLTTB, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx,
+                    out_cap, out_count, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int mmlttb_host_buffer_bytes(int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                             int binmode, size_t* bytes) {
+  if (!bytes) return MMLTTB_EINVAL;
+  HostLayout l;
+  int rc = host_layout(ydtype, xkind, n_in, n_out, r_ps, binmode, &l);
+  if (rc) return rc;
+  *bytes = l.total;
+  return MMLTTB_OK;
+}
+
+int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, int xkind,
+                           int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
+                           int64_t* out_host, int64_t out_cap, int64_t* out_count_host,
+                           void* device_buffer, size_t device_bytes, mmlttb_stream stream) {
+  HostLayout l;
+  int rc = host_layout(ydtype, xkind, n_in, n_out, r_ps, binmode, &l);
+  if (rc) return rc;
+  if (n_in > 0 && y_host == nullptr) return MMLTTB_EINVAL;
+  if (xkind != MMLTTB_X_IMPLICIT && n_in > 0 && x_host == nullptr) return MMLTTB_EINVAL;
+  const int64_t need = n_out < n_in ? n_out : n_in;
+  if (need > 0 && out_host == nullptr) return MMLTTB_EINVAL;
+  if (out_cap < need) return MMLTTB_ERANGE;
+  if (device_buffer == nullptr || device_bytes < l.total) return MMLTTB_ENOSPC;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* b = (char*)device_buffer;
+  const size_t es = ydtype == MMLTTB_F32 ? 4 : 8;
+  cudaError_t e;
+  if (n_in > 0 && (e = cudaMemcpyAsync(b + l.y, y_host, (size_t)n_in * es, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e);
+  if (xkind != MMLTTB_X_IMPLICIT && n_in > 0 &&
+      (e = cudaMemcpyAsync(b + l.x, x_host, (size_t)n_in * 8, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e);
+  rc = run_single(MMLTTB_OP_MINMAXLTTB, b + l.y, ydtype, xkind == MMLTTB_X_IMPLICIT ? nullptr : b + l.x,
+                  xkind, n_in, n_out, r_ps, binmode, (int64_t*)(b + l.out), out_cap < need ? out_cap : need,
+                  (int64_t*)(b + l.count), b + l.ws, l.ws_bytes, st);
+  if (rc) return rc;
+  if (need > 0 && (e = cudaMemcpyAsync(out_host, b + l.out, (size_t)need * 8, cudaMemcpyDeviceToHost, st)))
+    return cuda_fail(e);
+  if (out_count_host && (e = cudaMemcpyAsync(out_count_host, b + l.count, 8, cudaMemcpyDeviceToHost, st)))
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+  return MMLTTB_OK;
+}
+
+int mmlttb_set_timing_events(void* start_event, void* stop_event) {
+  g_ev_start = (cudaEvent_t)start_event;
+  g_ev_stop = (cudaEvent_t)stop_event;
+  return MMLTTB_OK;
+}
+
+unsigned long long mmlttb_launch_count(void) { return g_launches; }
+
+int mmlttb_workspace_status(const void* workspace, int* status, mmlttb_stream stream) {
+  if (!workspace || !status) return MMLTTB_EINVAL;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, workspace, sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  *status = (int)v;
+  return MMLTTB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// Shared structures and device helpers of libmmlttb (MinMaxLTTB, arXiv 2305.00332).
+//
+// One launch sequence serves a single series and a batch of series alike: every
+// kernel receives a `Batch` holding the per-series plans, and the MinMax stream
+// walks one global "interior position" space that concatenates the interior points
+// 1..n-2 of every series that needs preselection.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <stdint.h>
+
+#include "mmlttb.h"
+
+namespace mmlttb {
+
+// What a series needs, decided on the host from its sizes alone (Sec. 3).
+enum Branch : int32_t {
+  BR_ARANGE = 0,       // n_out >= n: every index
+  BR_LTTB_ALL = 1,     // LTTB on all n points (plain LTTB, or r_ps*n_out >= n)
+  BR_MINMAX_LTTB = 2,  // MinMax preselection, then LTTB on the preselected points
+  BR_PRESELECT = 3,    // MinMax preselection only; the list goes to the output
+};
+
+// Which LTTB engine resolves the serial bucket chain.
+enum Engine : int32_t {
+  EN_NONE = 0,
+  EN_TABLES = 1,  // per-position transition tables + parallel chain composition
+  EN_GRID = 2,    // one grid-wide step per bucket (cooperative launch)
+  EN_BLOCK = 3,   // one CTA per series, one block-wide step per bucket
+};
+
+// Largest LTTB bucket (in points) the transition-table engine accepts.
+constexpr int kTableMaxBucket = 32;
+// Threads of the streaming MinMax kernel's CTAs.
+constexpr int kStreamThreads = 256;
+constexpr int kStreamWarps = kStreamThreads / 32;
+
+// Result of one warp over one bin (or the part of a bin inside the warp's range):
+// order-preserving integer keys of the extreme y values and their point indices.
+struct Record {
+  long long kmin, kmax;
+  long long imin, imax;
+};
+
+struct SeriesPlan {
+  const void* y;
+  const void* x;
+  int32_t ydt, xk, binmode, branch, engine, r_ps;
+  int64_t n, n_out;
+  int64_t B;         // MinMax bins (minmax branches), else 0
+  int64_t bin_off;   // global index of this series' bin 0 in the record space
+  int64_t edge_off;  // index of this series' S_0 in the edge array (x-width bins)
+  int64_t pos_off;   // global interior position of point 1
+  int64_t npos;      // interior points in the global position space (n-2 or 0)
+  int64_t tab_off;   // first slot of this series in the table-slot space
+  int64_t tab_cap;   // slots reserved (positions that may need a table entry)
+  int64_t* sel;      // preselected list (capacity 2B+2), NULL for BR_LTTB_ALL
+  int64_t* m_ptr;    // number of preselected points (device), minmax branches
+  uint8_t* tab;      // one transition-table byte per position (EN_TABLES)
+  double* means;     // 2*K doubles: next-bucket means (EN_GRID / EN_BLOCK)
+  int64_t* out;
+  int64_t* out_count;
+};
+
+struct Batch {
+  const SeriesPlan* plans;  // device array of n_series plans; NULL: the single plan `one`
+  SeriesPlan one;
+  const int64_t* pos_offs;   // n_series+1 prefix of npos (NULL for a single series)
+  const int64_t* edge_offs;  // n_series+1 prefix of edge counts
+  const int64_t* tab_offs;   // n_series+1 prefix of tab_cap
+  int32_t n_series;
+  int64_t total_pos;   // sum of npos
+  int64_t n_warps;     // streaming warps, each with at least one interior point
+  int64_t total_edges; // sum over x-width series of B+1
+  int64_t total_slots; // sum of tab_cap
+  Record* rec;         // total bins + n_warps records
+  int64_t* edges;      // bin starts S_b of x-width series
+  unsigned* status;    // error bits (1: a bounded wait timed out, 2: device check failed)
+  unsigned* barrier;   // grid barrier counter (EN_GRID)
+  double* partial;     // 2 x grid x (area, position) partials (EN_GRID)
+};
+
+__host__ __device__ inline const SeriesPlan& plan_of(const Batch& bt, int s) {
+  return bt.plans ? bt.plans[s] : bt.one;
+}
+
+// Last index i in [0, count) with offs[i] <= v (offs non-decreasing, offs[0] <= v).
+__device__ inline int upper_index(const int64_t* offs, int count, int64_t v) {
+  int lo = 0, hi = count;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (offs[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// floor(a*b/c) for a, b >= 0, c > 0, exact for any int64 inputs whose quotient fits.
+__host__ __device__ inline int64_t muldiv(int64_t a, int64_t b, int64_t c) {
+#ifdef __CUDA_ARCH__
+  unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  unsigned long long hi = __umul64hi((unsigned long long)a, (unsigned long long)b);
+  if (hi == 0) return (int64_t)(lo / (unsigned long long)c);
+  unsigned __int128 num = ((unsigned __int128)hi << 64) | lo;
+  return (int64_t)(num / (unsigned long long)c);
+#else
+  unsigned __int128 num = (unsigned __int128)(uint64_t)a * (uint64_t)b;
+  return (int64_t)(num / (uint64_t)c);
+#endif
+}
+
+// Start of part j when `items` items are split into `parts` equal-count parts,
+// counting from 1: floor(j*items/parts)+1.  Used for MinMax index bins over the
+// interior points and for LTTB buckets over the interior positions.
+__host__ __device__ inline int64_t part_start(int64_t j, int64_t items, int64_t parts) {
+  return muldiv(j, items, parts) + 1;
+}
+
+// The part that contains position p (1 <= p <= items): the largest j with
+// part_start(j) <= p, i.e. floor((p*parts - 1) / items).
+__host__ __device__ inline int64_t part_of(int64_t p, int64_t items, int64_t parts) {
+#ifdef __CUDA_ARCH__
+  unsigned long long lo = (unsigned long long)p * (unsigned long long)parts;
+  unsigned long long hi = __umul64hi((unsigned long long)p, (unsigned long long)parts);
+  if (hi == 0) return (int64_t)((lo - 1ull) / (unsigned long long)items);
+  unsigned __int128 num = (((unsigned __int128)hi << 64) | lo) - 1u;
+  return (int64_t)(num / (unsigned long long)items);
+#else
+  unsigned __int128 num = (unsigned __int128)(uint64_t)p * (uint64_t)parts - 1u;
+  return (int64_t)(num / (uint64_t)items);
+#endif
+}
+
+// Streaming warp w covers global interior positions [floor(w*T/W), floor((w+1)*T/W)).
+__host__ __device__ inline int64_t warp_begin(int64_t w, int64_t total, int64_t warps) {
+  return muldiv(w, total, warps);
+}
+// The warp whose range holds global position g: floor(((g+1)*W - 1) / T).
+__host__ __device__ inline int64_t warp_of(int64_t g, int64_t total, int64_t warps) {
+  return part_of(g + 1, total, warps);
+}
+
+// Order-preserving integer keys of y values; -0.0 and +0.0 share key 0.
+__device__ __forceinline__ int key32(float v) {
+  int s = __float_as_int(v);
+  return s >= 0 ? s : -(s & 0x7fffffff);
+}
+__device__ __forceinline__ long long key64(double v) {
+  long long s = __double_as_longlong(v);
+  return s >= 0 ? s : -(s & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
+  if (status) atomicOr(status, bit);
+}
+
+// Coordinates of original point i as FP64 (implicit x is the index).
+__device__ __forceinline__ double x_of(const SeriesPlan& sp, int64_t i) {
+  if (sp.xk == MMLTTB_X_IMPLICIT) return (double)i;
+  if (sp.xk == MMLTTB_X_I64) return (double)__ldg((const long long*)sp.x + i);
+  return __ldg((const double*)sp.x + i);
+}
+__device__ __forceinline__ double y_of(const SeriesPlan& sp, int64_t i) {
+  if (sp.ydt == MMLTTB_F32) return (double)__ldg((const float*)sp.y + i);
+  return __ldg((const double*)sp.y + i);
+}
+// Original index of LTTB position p (identity when LTTB runs on all points).
+__device__ __forceinline__ int64_t index_of(const SeriesPlan& sp, int64_t p) {
+  return sp.sel ? sp.sel[p] : p;
+}
+
+// LTTB triangle area (Sec. 2.2.1): |(xa-xc)(yb-ya) - (xa-xb)(yc-ya)|, every
+// operation rounded on its own (no contraction into FMA).
+__device__ __forceinline__ double tri_area(double xa, double ya, double xb, double yb,
+                                           double xc, double yc) {
+  double p1 = __dmul_rn(__dsub_rn(xa, xc), __dsub_rn(yb, ya));
+  double p2 = __dmul_rn(__dsub_rn(xa, xb), __dsub_rn(yc, ya));
+  return fabs(__dsub_rn(p1, p2));
+}
+
+// ---- host launchers (defined in minmax.cu / lttb.cu) ----
+cudaError_t launch_edges(const Batch& bt, cudaStream_t st);
+cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st);
+cudaError_t launch_merge(const Batch& bt, int n_blocks, cudaStream_t st);
+cudaError_t launch_tables(const Batch& bt, cudaStream_t st);
+cudaError_t launch_chain(const Batch& bt, int n_blocks, cudaStream_t st);
+cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_t st);
+cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st);
+cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st);
+int stream_blocks_per_sm();
+int lttb_grid_blocks_per_sm();
+constexpr int kGridThreads = 256;
+
+}  // namespace mmlttb

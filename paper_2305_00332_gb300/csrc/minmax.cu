@@ -1,0 +1,391 @@
+// MinMax preselection kernels (Sec. 3 first step; MinMax of Sec. 2.2.1, Table 1).
+//
+//  k_edges   x-width bins: one warp per bin edge, 32-ary search for the first
+//            interior point with x >= e_b (x is non-decreasing).
+//  k_stream  the HBM-bound pass.  The interior points of every series are laid end
+//            to end in one global position space, cut into W equal ranges, one per
+//            warp.  A warp walks the bins that meet its range; for each piece it
+//            streams y with 16-byte coalesced loads (4 in flight per lane) and keeps
+//            a per-lane first-occurrence argmin/argmax, then reduces across the warp
+//            and writes one Record at slot (global bin + warp).  x is never streamed:
+//            bin bounds come from integer arithmetic (index bins) or from k_edges.
+//  k_merge   one CTA per series: combines the records of each bin (they sit in
+//            consecutive slots), drops empty bins, dedupes argmin == argmax and
+//            compacts [0, per-bin pairs..., n-1] with a block-wide scan.
+#include "common.cuh"
+
+namespace mmlttb {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUnroll = 4;  // 16-byte vectors in flight per lane
+
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream4u(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// NaN-propagating float min/max (a NaN operand makes the result NaN).
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// The high 32 bits of a double read as a float.  For doubles below 2^1017 in
+// magnitude this is a non-decreasing function of the double's value (the bit
+// patterns of both formats order like sign-magnitude integers), so
+// proxy(e) > proxy(m) implies e > m.  Larger magnitudes, inf and NaN map to NaN or
+// inf proxies, which the callers treat as "compare exactly".
+__device__ __forceinline__ float proxy_of_hi(unsigned hi) { return __uint_as_float(hi); }
+
+// Bin bounds of series sp (R2 index bins; R3 x-width bins via the edge array).
+__device__ __forceinline__ int64_t bin_start(const Batch& bt, const SeriesPlan& sp, int64_t b) {
+  if (sp.binmode == MMLTTB_BINS_INDEX) return part_start(b, sp.n - 2, sp.B);
+  return bt.edges[sp.edge_off + b];
+}
+__device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesPlan& sp, int64_t p) {
+  if (sp.binmode == MMLTTB_BINS_INDEX) return part_of(p, sp.n - 2, sp.B);
+  return upper_index(bt.edges + sp.edge_off, (int)sp.B, p);
+}
+
+// Warp-wide first-occurrence argmin/argmax of y[lo, hi) for float32 y.
+__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  const float v0 = __ldg(y + lo);  // every lane starts from the first point (offset 0)
+  float mn = v0, mx = v0;
+  uint32_t omn = 0, omx = 0;
+  const uintptr_t ybase = (uintptr_t)y;
+  const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
+  const uintptr_t aend = ybase + (uintptr_t)hi * 4u;
+  const int64_t nvec = (int64_t)((aend - a0 + 15u) >> 4);
+  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 4 - lo);  // in [-3, 0]
+  const float4* vp = (const float4*)a0;
+  const float inf = __int_as_float(0x7f800000);
+  for (int64_t v = lane; v < nvec; v += 32 * kUnroll) {
+    float4 buf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + 32 * u;
+      if (vi < nvec) buf[u] = ld_stream4(vp + vi);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + 32 * u;
+      if (vi < nvec) {
+        const int32_t r = rel0 + 4 * (int32_t)vi;
+        const float e[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
+        float fm[4], fx[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const bool ok = (uint32_t)(r + k) < len;
+          fm[k] = ok ? e[k] : inf;
+          fx[k] = ok ? e[k] : -inf;
+        }
+        const float m4 = fminf(fminf(fm[0], fm[1]), fminf(fm[2], fm[3]));
+        const float x4 = fmaxf(fmaxf(fx[0], fx[1]), fmaxf(fx[2], fx[3]));
+        if (m4 < mn) {  // rare: some element is a new strict minimum
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (fm[k] < mn) { mn = fm[k]; omn = (uint32_t)(r + k); }
+        }
+        if (x4 > mx) {
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (fx[k] > mx) { mx = fx[k]; omx = (uint32_t)(r + k); }
+        }
+      }
+    }
+  }
+  const int kmn = key32(mn), kmx = key32(mx);
+  const int wmn = __reduce_min_sync(kFull, kmn);
+  const unsigned wo = __reduce_min_sync(kFull, kmn == wmn ? omn : 0xffffffffu);
+  const int wmx = __reduce_max_sync(kFull, kmx);
+  const unsigned wx = __reduce_min_sync(kFull, kmx == wmx ? omx : 0xffffffffu);
+  Record r;
+  r.kmin = wmn;
+  r.kmax = wmx;
+  r.imin = lo + (int64_t)wo;
+  r.imax = lo + (int64_t)wx;
+  return r;
+}
+
+// Warp-wide first-occurrence argmin/argmax of y[lo, hi) for float64 y.  The hot
+// loop issues no FP64 instruction (FP64 is a narrow pipe on this part): a float
+// compare of the high-word proxies rules out almost every element, and the rest
+// are compared exactly through order-preserving int64 keys.
+__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  const long long b0 = __double_as_longlong(__ldg(y + lo));
+  long long kmn = key64(__longlong_as_double(b0)), kmx = kmn;
+  float pmn = proxy_of_hi((unsigned)(b0 >> 32)), pmx = pmn;
+  uint32_t omn = 0, omx = 0;
+  const uintptr_t ybase = (uintptr_t)y;
+  const uintptr_t a0 = (ybase + (uintptr_t)lo * 8u) & ~(uintptr_t)15;
+  const uintptr_t aend = ybase + (uintptr_t)hi * 8u;
+  const int64_t nvec = (int64_t)((aend - a0 + 15u) >> 4);
+  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 8 - lo);  // in [-1, 0]
+  const float inf = __int_as_float(0x7f800000);
+  for (int64_t v = lane; v < nvec; v += 32 * kUnroll) {
+    uint4 buf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + 32 * u;
+      if (vi < nvec) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u));
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + 32 * u;
+      if (vi < nvec) {
+        const int32_t r = rel0 + 2 * (int32_t)vi;
+        const bool ok0 = (uint32_t)r < len, ok1 = (uint32_t)(r + 1) < len;
+        const float p0 = proxy_of_hi(buf[u].y), p1 = proxy_of_hi(buf[u].w);
+        const float pm = fmin_nan(ok0 ? p0 : inf, ok1 ? p1 : inf);
+        const float px = fmax_nan(ok0 ? p0 : -inf, ok1 ? p1 : -inf);
+        const bool need_min = !(pm > pmn);
+        const bool need_max = !(px < pmx);
+        if (need_min || need_max) {  // rare: exact comparison through int64 keys
+          const long long e0 = ((long long)buf[u].y << 32) | buf[u].x;
+          const long long e1 = ((long long)buf[u].w << 32) | buf[u].z;
+          const long long k0 = key64(__longlong_as_double(e0));
+          const long long k1 = key64(__longlong_as_double(e1));
+          if (ok0 && k0 < kmn) { kmn = k0; omn = (uint32_t)r; pmn = p0; }
+          if (ok1 && k1 < kmn) { kmn = k1; omn = (uint32_t)(r + 1); pmn = p1; }
+          if (ok0 && k0 > kmx) { kmx = k0; omx = (uint32_t)r; pmx = p0; }
+          if (ok1 && k1 > kmx) { kmx = k1; omx = (uint32_t)(r + 1); pmx = p1; }
+        }
+      }
+    }
+  }
+  // int64 order = (signed high word, unsigned low word)
+  const int hmn = (int)(kmn >> 32);
+  const unsigned lmn = (unsigned)kmn;
+  const int whm = __reduce_min_sync(kFull, hmn);
+  const unsigned wlm = __reduce_min_sync(kFull, hmn == whm ? lmn : 0xffffffffu);
+  const bool eqm = (hmn == whm) && (lmn == wlm);
+  const unsigned wo = __reduce_min_sync(kFull, eqm ? omn : 0xffffffffu);
+  const int hmx = (int)(kmx >> 32);
+  const unsigned lmx = (unsigned)kmx;
+  const int whx = __reduce_max_sync(kFull, hmx);
+  const unsigned wlx = __reduce_max_sync(kFull, hmx == whx ? lmx : 0u);
+  const bool eqx = (hmx == whx) && (lmx == wlx);
+  const unsigned wx = __reduce_min_sync(kFull, eqx ? omx : 0xffffffffu);
+  Record r;
+  r.kmin = ((long long)whm << 32) | wlm;
+  r.kmax = ((long long)whx << 32) | wlx;
+  r.imin = lo + (int64_t)wo;
+  r.imax = lo + (int64_t)wx;
+  return r;
+}
+
+// One warp over the interior points [p_lo, p_hi) of one series.
+__device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t p_lo,
+                                  int64_t p_hi, int64_t w, int lane) {
+  int64_t b = bin_containing(bt, sp, p_lo);
+  for (;;) {
+    const int64_t sb = bin_start(bt, sp, b);
+    const int64_t sb1 = (b + 1 >= sp.B) ? sp.n - 1 : bin_start(bt, sp, b + 1);
+    const int64_t lo = sb > p_lo ? sb : p_lo;
+    const int64_t hi = sb1 < p_hi ? sb1 : p_hi;
+    if (lo < hi) {
+      Record r = (sp.ydt == MMLTTB_F32) ? segment_f32((const float*)sp.y, lo, hi, lane)
+                                        : segment_f64((const double*)sp.y, lo, hi, lane);
+      if (lane == 0) bt.rec[sp.bin_off + b + w] = r;
+    }
+    if (sb1 >= p_hi || b + 1 >= sp.B) break;
+    ++b;
+  }
+}
+
+__global__ void __launch_bounds__(kStreamThreads) k_stream(const __grid_constant__ Batch bt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  if (w >= bt.n_warps) return;
+  int64_t g = warp_begin(w, bt.total_pos, bt.n_warps);
+  const int64_t g_end = warp_begin(w + 1, bt.total_pos, bt.n_warps);
+  int s = bt.pos_offs ? upper_index(bt.pos_offs, bt.n_series, g) : 0;
+  while (g < g_end && s < bt.n_series) {
+    const SeriesPlan& sp = plan_of(bt, s);
+    const int64_t send = sp.pos_off + sp.npos;
+    const int64_t seg_end = send < g_end ? send : g_end;
+    if (seg_end > g) {
+      warp_series_range(bt, sp, 1 + (g - sp.pos_off), 1 + (seg_end - sp.pos_off), w, lane);
+      g = seg_end;
+    }
+    ++s;
+  }
+}
+
+// One warp per bin edge of every x-width series: S_b = first interior point with
+// x >= e_b, e_b = x_0 + floor(b (x_{n-1} - x_0) / B) (R3); S_0 = 1, S_B = n-1.
+__global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= bt.total_edges) return;
+  const int s = bt.edge_offs ? upper_index(bt.edge_offs, bt.n_series, e) : 0;
+  const SeriesPlan& sp = plan_of(bt, s);
+  const int64_t b = e - sp.edge_off;
+  int64_t res;
+  if (sp.n < 3 || b == 0) {
+    res = 1;
+  } else if (b >= sp.B) {
+    res = sp.n - 1;
+  } else {
+    const long long* x = (const long long*)sp.x;
+    const long long x0 = __ldg(x), xl = __ldg(x + sp.n - 1);
+    const long long D = xl - x0;
+    const long long eb = x0 + (long long)muldiv(b, D, sp.B);
+    int64_t lo = 1, hi = sp.n - 1;  // answer in [lo, hi]
+    while (hi - lo > 32) {
+      const int64_t step = (hi - lo + 31) / 32;
+      const int64_t q = lo + (int64_t)lane * step;
+      const bool pred = q < hi && __ldg(x + q) >= eb;
+      const unsigned m = __ballot_sync(kFull, pred);
+      if (m == 0) {
+        const int64_t last = lo + ((hi - lo - 1) / step) * step;  // last sampled point
+        lo = last + 1;
+      } else {
+        const int f = __ffs(m) - 1;
+        const int64_t qf = lo + (int64_t)f * step;
+        lo = f > 0 ? qf - step + 1 : lo;
+        hi = qf;
+      }
+    }
+    const int64_t q = lo + lane;
+    const bool pred = q < hi && __ldg(x + q) >= eb;
+    const unsigned m = __ballot_sync(kFull, pred);
+    res = m ? lo + (__ffs(m) - 1) : hi;
+  }
+  if (lane == 0) bt.edges[e] = res;
+}
+
+__device__ __forceinline__ void combine(Record& a, const Record& b) {
+  if (b.kmin < a.kmin || (b.kmin == a.kmin && b.imin < a.imin)) { a.kmin = b.kmin; a.imin = b.imin; }
+  if (b.kmax > a.kmax || (b.kmax == a.kmax && b.imax < a.imax)) { a.kmax = b.kmax; a.imax = b.imax; }
+}
+
+// Exclusive block scan of small non-negative counts; returns the block total.
+template <int NT>
+__device__ int block_excl_scan(int v, int* excl) {
+  __shared__ int wsum[NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int t = __shfl_up_sync(kFull, inc, d);
+    if (lane >= d) inc += t;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int u = __shfl_up_sync(kFull, t, d);
+      if (lane >= d) t += u;
+    }
+    if (lane < NT / 32) wsum[lane] = t;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const int before = wid > 0 ? wsum[wid - 1] : 0;
+  const int total = wsum[NT / 32 - 1];
+  *excl = before + inc - v;
+  __syncthreads();
+  return total;
+}
+
+constexpr int kMergeThreads = 1024;
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ Batch bt) {
+  const SeriesPlan& sp = plan_of(bt, blockIdx.x);
+  if (sp.branch != BR_MINMAX_LTTB && sp.branch != BR_PRESELECT) return;
+  int64_t* P = sp.sel;
+  const int64_t n = sp.n;
+  if (n <= 2) {  // no interior points: [0] or [0, 1]
+    if (threadIdx.x < n) P[threadIdx.x] = threadIdx.x;
+    if (threadIdx.x == 0) {
+      *sp.m_ptr = n;
+      if (sp.branch == BR_PRESELECT && sp.out_count) *sp.out_count = n;
+    }
+    return;
+  }
+  int64_t base = 0;
+  for (int64_t tile = 0; tile < sp.B; tile += kMergeThreads) {
+    const int64_t b = tile + threadIdx.x;
+    int cnt = 0;
+    int64_t lo_i = 0, hi_i = 0;
+    if (b < sp.B) {
+      const int64_t sb = bin_start(bt, sp, b);
+      const int64_t sb1 = (b + 1 >= sp.B) ? n - 1 : bin_start(bt, sp, b + 1);
+      if (sb < sb1) {
+        const int64_t wf = warp_of(sp.pos_off + sb - 1, bt.total_pos, bt.n_warps);
+        const int64_t wl = warp_of(sp.pos_off + sb1 - 2, bt.total_pos, bt.n_warps);
+        const Record* rb = bt.rec + sp.bin_off + b;
+        Record r = rb[wf];
+        for (int64_t w = wf + 1; w <= wl; ++w) combine(r, rb[w]);
+        lo_i = r.imin < r.imax ? r.imin : r.imax;
+        hi_i = r.imin < r.imax ? r.imax : r.imin;
+        cnt = lo_i == hi_i ? 1 : 2;
+      }
+    }
+    int excl;
+    const int total = block_excl_scan<kMergeThreads>(cnt, &excl);
+    if (cnt > 0) P[1 + base + excl] = lo_i;
+    if (cnt > 1) P[2 + base + excl] = hi_i;
+    base += total;
+  }
+  if (threadIdx.x == 0) {
+    P[0] = 0;
+    P[1 + base] = n - 1;
+    *sp.m_ptr = base + 2;
+    if (sp.branch == BR_PRESELECT && sp.out_count) *sp.out_count = base + 2;
+  }
+}
+
+}  // namespace
+
+int stream_blocks_per_sm() {
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_stream, kStreamThreads, 0) != cudaSuccess)
+    return 1;
+  return bps > 0 ? bps : 1;
+}
+
+cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
+  if (bt.total_edges <= 0) return cudaSuccess;
+  const int64_t threads = bt.total_edges * 32;
+  const int64_t grid = (threads + 255) / 256;
+  k_edges<<<(unsigned)grid, 256, 0, st>>>(bt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st) {
+  if (bt.n_warps <= 0) return cudaSuccess;
+  k_stream<<<(unsigned)grid, kStreamThreads, 0, st>>>(bt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const Batch& bt, int n_blocks, cudaStream_t st) {
+  if (n_blocks <= 0) return cudaSuccess;
+  k_merge<<<n_blocks, kMergeThreads, 0, st>>>(bt);
+  return cudaGetLastError();
+}
+
+}  // namespace mmlttb

@@ -1,0 +1,71 @@
+"""The C ABI without a GPU: the library loads, exports every entry point that
+include/mmlttb.h declares, and rejects bad arguments on the host before it would
+touch a device (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "mmlttb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mmlttb_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib(libpath):
+    return ctypes.CDLL(libpath)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("mmlttb_minmax_preselect", "mmlttb_lttb", "mmlttb_minmaxlttb",
+                     "mmlttb_workspace_bytes", "mmlttb_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version(lib):
+    lib.mmlttb_strerror.restype = ctypes.c_char_p
+    assert lib.mmlttb_strerror(0) == b"success"
+    assert lib.mmlttb_strerror(-1) == b"invalid argument"
+    assert lib.mmlttb_strerror(-2) == b"workspace too small"
+    assert lib.mmlttb_strerror(12345) == b"unknown error"
+    assert lib.mmlttb_version() >= 100
+
+
+def _call_minmaxlttb(lib, y, ydt, x, xk, n, n_out, r_ps, binmode, out, cap):
+    f = lib.mmlttb_minmaxlttb
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                  ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    return f(y, ydt, x, xk, n, n_out, r_ps, binmode, out, cap, None, None, 0, None)
+
+
+@pytest.mark.parametrize("args,code", [
+    # (y, ydt, x, xk, n, n_out, r_ps, binmode, out, cap)
+    ((1, 0, None, 0, 100, 10, 1, 0, 1, 10), -1),     # r_ps < 2
+    ((1, 0, None, 0, 100, 2, 4, 0, 1, 10), -1),      # n_out < 3
+    ((1, 7, None, 0, 100, 10, 4, 0, 1, 10), -1),     # bad dtype
+    ((1, 0, None, 9, 100, 10, 4, 0, 1, 10), -1),     # bad x kind
+    ((1, 0, None, 0, 100, 10, 4, 5, 1, 10), -1),     # bad bin mode
+    ((1, 0, None, 0, 100, 10, 4, 1, 1, 10), -1),     # x-width bins need int64 x
+    ((1, 0, None, 1, 100, 10, 4, 0, 1, 10), -1),     # int64 x but NULL pointer
+    ((None, 0, None, 0, 100, 10, 4, 0, 1, 10), -1),  # NULL y
+    ((1, 0, None, 0, -5, 10, 4, 0, 1, 10), -1),      # negative n
+    ((1, 0, None, 0, 100, 10, 4, 0, 1, 9), -6),      # output capacity too small
+    ((1, 0, None, 0, 100, 10, 4, 0, None, 10), -1),  # NULL output
+])
+def test_host_side_validation(lib, args, code):
+    assert _call_minmaxlttb(lib, *args) == code

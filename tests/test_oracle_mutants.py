@@ -31,7 +31,7 @@ MUTANTS = [
     ("minmax_includes_last_point", "for (int64_t p = 1; p <= n - 2; p++) {", "for (int64_t p = 1; p <= n - 1; p++) {"),
     ("last_point_dropped", "    out[m++] = n - 1;\n", "\n"),
     ("no_dedupe_equal_extrema", "if (hi != lo) out[m++] = hi;", "out[m++] = hi;"),
-    ("xwidth_edge_strict", "(__int128)x0 + q <= (__int128)xi[p]", "(__int128)x0 + q < (__int128)xi[p]"),
+    ("bin_edge_strict", "while (next <= here) {", "while (next < here) {"),
     ("bins_from_r_ps_not_halved", "int64_t B = n_out * (int64_t)r_ps / 2;\n    if (B < 1) return MMO_EINVAL;",
      "int64_t B = n_out * (int64_t)r_ps;\n    if (B < 1) return MMO_EINVAL;"),
     ("no_lttb_when_rps_covers_n", "if ((int64_t)r_ps * n_out >= n) return mmo_lttb(y, ydt, x, xk, n, n_out, out);", ""),
