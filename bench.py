@@ -215,6 +215,9 @@ def main():
     # per-step events around the streaming MinMax kernel (the dominant kernel)
     K = args.steps
     k_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in k_ev:  # torch creates the CUDA events on first record
+        a.record(stream)
+        b.record(stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     clocks = ClockSampler(vis[local] if local < len(vis) else str(local))
