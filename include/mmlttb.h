@@ -45,6 +45,7 @@ extern "C" {
 #define MMLTTB_ETIMEOUT (-4) /* a bounded device-side wait gave up (status word) */
 #define MMLTTB_ERANGE (-6)   /* output capacity too small */
 #define MMLTTB_EDEVICE (-7)  /* a device-side check failed (status word) */
+#define MMLTTB_ENOMEM (-8)   /* host memory for a batch object could not be allocated */
 
 /* Element type of y. */
 #define MMLTTB_F32 0
@@ -147,6 +148,48 @@ int mmlttb_minmaxlttb_host(const void *y_host, int ydtype, const void *x_host, i
                            int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
                            int64_t *out_host, int64_t out_cap, int64_t *out_count_host,
                            void *device_buffer, size_t device_bytes, mmlttb_stream stream);
+
+/*
+ * Batches (many series in one launch sequence).  Each series is described by a
+ * mmlttb_series_desc; its op selects MinMaxLTTB, plain LTTB or preselection only,
+ * with the same semantics and argument rules as the single-series entry points.
+ * All series run in one sequence of kernels: one MinMax stream over the interior
+ * points of every series (cut into equal slices, one per warp, whatever the series
+ * lengths), then per-series compaction, LTTB tables and chains.  The batch object
+ * owns a pinned host copy of its plan table (allocated by mmlttb_batch_create,
+ * freed by mmlttb_batch_destroy); device memory is the caller's workspace.
+ */
+typedef struct mmlttb_series_desc {
+  const void *y;      /* device: n_in float32/float64 values */
+  const void *x;      /* device: n_in int64/float64 values, or NULL with MMLTTB_X_IMPLICIT */
+  int32_t op;         /* MMLTTB_OP_MINMAXLTTB, MMLTTB_OP_LTTB or MMLTTB_OP_PRESELECT */
+  int32_t ydtype;     /* MMLTTB_F32 / MMLTTB_F64 */
+  int32_t xkind;      /* MMLTTB_X_* */
+  int32_t binmode;    /* MMLTTB_BINS_* */
+  int32_t r_ps;
+  int32_t reserved;   /* set to 0 */
+  int64_t n_in, n_out;
+  int64_t *out_idx;   /* device int64[out_cap] */
+  int64_t out_cap;
+  int64_t *out_count; /* device int64, nullable */
+} mmlttb_series_desc;
+
+typedef struct mmlttb_batch *mmlttb_batch_t;
+
+/* Validate and plan n_series series (host side; reads only the descriptors).
+   Returns MMLTTB_EINVAL / MMLTTB_ERANGE for the first invalid series. */
+int mmlttb_batch_create(const mmlttb_series_desc *descs, int64_t n_series, mmlttb_batch_t *out);
+/* Workspace bytes the batch needs (on the device current at creation). */
+int mmlttb_batch_workspace_bytes(mmlttb_batch_t batch, size_t *bytes);
+/* Enqueue the batch on `stream` (asynchronous; capturable into a CUDA graph). */
+int mmlttb_batch_run(mmlttb_batch_t batch, void *workspace, size_t workspace_bytes,
+                     mmlttb_stream stream);
+/* Same work through a CUDA graph captured on the first call (per workspace address)
+   and replayed afterwards: one graph launch instead of about six API calls. */
+int mmlttb_batch_run_graph(mmlttb_batch_t batch, void *workspace, size_t workspace_bytes,
+                           mmlttb_stream stream);
+/* Release the batch (its graph and pinned plan table).  No call may be in flight. */
+int mmlttb_batch_destroy(mmlttb_batch_t batch);
 
 /*
  * Profiling hook (per calling thread, one shot): the next call that runs MinMax

@@ -15,7 +15,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmmlttb.so")
 
-OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE = 0, -1, -2, -3, -4, -6, -7
+OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE, ENOMEM = 0, -1, -2, -3, -4, -6, -7, -8
 F32, F64 = 0, 1
 X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1
@@ -126,9 +126,7 @@ def workspace_bytes(op, ydtype, xkind, n_in, n_out, r_ps=2, binmode=BINS_INDEX):
 def _workspace(nbytes, device, workspace):
     if workspace is None:
         return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
-    if workspace.numel() * workspace.element_size() < nbytes:
-        raise ValueError("workspace too small")
-    return workspace
+    return workspace  # the C ABI checks the size (MMLTTB_ENOSPC)
 
 
 def _finish(out, count, sync):
@@ -150,7 +148,7 @@ def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, works
     ws = _workspace(workspace_bytes(OP_PRESELECT, yd, xk, n, n_out, r_ps, bm), y.device, workspace)
     _check(lib.mmlttb_minmax_preselect(
         y.data_ptr(), yd, x.data_ptr() if x is not None else None, xk, n, n_out, r_ps, bm,
-        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(y.device)),
+        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(), _stream(y.device)),
         "mmlttb_minmax_preselect")
     return _finish(out, count, sync)
 
@@ -167,7 +165,7 @@ def lttb(y, n_out, x=None, out=None, workspace=None, sync=True):
     ws = _workspace(workspace_bytes(OP_LTTB, yd, xk, n, n_out), y.device, workspace)
     _check(lib.mmlttb_lttb(
         y.data_ptr(), yd, x.data_ptr() if x is not None else None, xk, n, n_out,
-        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(y.device)),
+        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(), _stream(y.device)),
         "mmlttb_lttb")
     return _finish(out, count, sync)
 
@@ -185,7 +183,7 @@ def minmaxlttb(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, workspace
     ws = _workspace(workspace_bytes(OP_MINMAXLTTB, yd, xk, n, n_out, r_ps, bm), y.device, workspace)
     _check(lib.mmlttb_minmaxlttb(
         y.data_ptr(), yd, x.data_ptr() if x is not None else None, xk, n, n_out, r_ps, bm,
-        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(y.device)),
+        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(), _stream(y.device)),
         "mmlttb_minmaxlttb")
     return _finish(out, count, sync)
 
@@ -232,7 +230,8 @@ def minmaxlttb_host(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, devi
 
 def set_timing_events(start, stop):
     """Arm the one-shot events around the next streaming MinMax kernel
-    (torch.cuda.Event(enable_timing=True) objects, or None, None)."""
+    (torch.cuda.Event(enable_timing=True) objects that have been recorded once, so
+    that torch has created them; or None, None)."""
     _check(lib.mmlttb_set_timing_events(ctypes.c_void_p(start.cuda_event) if start is not None else None,
                                         ctypes.c_void_p(stop.cuda_event) if stop is not None else None),
            "mmlttb_set_timing_events")
@@ -241,3 +240,97 @@ def set_timing_events(start, stop):
 def launch_count():
     """Kernels launched by the library from this thread so far."""
     return int(lib.mmlttb_launch_count())
+
+
+class SeriesDesc(ctypes.Structure):
+    """mmlttb_series_desc."""
+    _fields_ = [("y", _vp), ("x", _vp), ("op", _i32), ("ydtype", _i32), ("xkind", _i32),
+                ("binmode", _i32), ("r_ps", _i32), ("reserved", _i32), ("n_in", _i64),
+                ("n_out", _i64), ("out_idx", _vp), ("out_cap", _i64), ("out_count", _vp)]
+
+
+lib.mmlttb_batch_create.restype = _int
+lib.mmlttb_batch_create.argtypes = [ctypes.POINTER(SeriesDesc), _i64, ctypes.POINTER(_vp)]
+lib.mmlttb_batch_workspace_bytes.restype = _int
+lib.mmlttb_batch_workspace_bytes.argtypes = [_vp, ctypes.POINTER(_sz)]
+lib.mmlttb_batch_run.restype = _int
+lib.mmlttb_batch_run.argtypes = [_vp, _vp, _sz, _vp]
+lib.mmlttb_batch_run_graph.restype = _int
+lib.mmlttb_batch_run_graph.argtypes = [_vp, _vp, _sz, _vp]
+lib.mmlttb_batch_destroy.restype = _int
+lib.mmlttb_batch_destroy.argtypes = [_vp]
+
+_OPS = {"minmaxlttb": OP_MINMAXLTTB, "lttb": OP_LTTB, "preselect": OP_PRESELECT}
+
+
+class Batch:
+    """Many series in one launch sequence (mmlttb_batch_*).
+
+    series: list of dicts with keys y (CUDA tensor), n_out, and optionally x, r_ps
+    (default 4), op ("minmaxlttb" | "lttb" | "preselect"), binmode.  Outputs live in
+    one int64 tensor; results() slices them after a sync."""
+
+    def __init__(self, series, workspace=None):
+        if not series:
+            raise ValueError("empty batch")
+        self.device = series[0]["y"].device
+        self._keep = []
+        caps = []
+        descs = (SeriesDesc * len(series))()
+        for i, s in enumerate(series):
+            y, x = s["y"], s.get("x")
+            _check_inputs(y, x)
+            op = _OPS[s.get("op", "minmaxlttb")]
+            r_ps = int(s.get("r_ps", 4))
+            n, n_out = y.numel(), int(s["n_out"])
+            cap = min(n, (n_out * r_ps // 2) * 2 + 2) if op == OP_PRESELECT else min(n, n_out)
+            caps.append(max(cap, 0))
+            d = descs[i]
+            d.y = y.data_ptr()
+            d.x = x.data_ptr() if x is not None else None
+            d.op, d.ydtype, d.xkind = op, _ydt(y), _xkind(x)
+            d.binmode, d.r_ps, d.reserved = _binmode(s.get("binmode", BINS_INDEX)), r_ps, 0
+            d.n_in, d.n_out = n, n_out
+            self._keep.append((y, x))
+        offs = [0]
+        for c in caps:
+            offs.append(offs[-1] + c)
+        self.offsets = offs
+        self.out = torch.empty(max(offs[-1], 1), dtype=torch.int64, device=self.device)
+        self.counts = torch.zeros(len(series), dtype=torch.int64, device=self.device)
+        base, cbase = self.out.data_ptr(), self.counts.data_ptr()
+        for i in range(len(series)):
+            descs[i].out_idx = base + 8 * offs[i]
+            descs[i].out_cap = caps[i]
+            descs[i].out_count = cbase + 8 * i
+        self._descs = descs
+        h = _vp()
+        _check(lib.mmlttb_batch_create(descs, len(series), ctypes.byref(h)), "mmlttb_batch_create")
+        self._h = h
+        b = ctypes.c_size_t(0)
+        _check(lib.mmlttb_batch_workspace_bytes(h, ctypes.byref(b)), "mmlttb_batch_workspace_bytes")
+        self.workspace_bytes = b.value
+        self.workspace = workspace if workspace is not None else torch.empty(
+            self.workspace_bytes, dtype=torch.uint8, device=self.device)
+
+    def run(self, graph=False):
+        fn = lib.mmlttb_batch_run_graph if graph else lib.mmlttb_batch_run
+        _check(fn(self._h, self.workspace.data_ptr(),
+                  self.workspace.numel() * self.workspace.element_size(), _stream(self.device)),
+               "mmlttb_batch_run_graph" if graph else "mmlttb_batch_run")
+
+    def results(self):
+        counts = self.counts.cpu().tolist()
+        return [self.out[self.offsets[i]: self.offsets[i] + counts[i]] for i in range(len(counts))]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize(self.device)
+            lib.mmlttb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

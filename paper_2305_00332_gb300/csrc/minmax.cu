@@ -19,7 +19,14 @@ namespace mmlttb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kUnroll = 4;  // 16-byte vectors in flight per lane
+// Build-time tuning of the stream kernel (swept on the target; see the profiles).
+#ifndef MMLTTB_STREAM_UNROLL
+#define MMLTTB_STREAM_UNROLL 4
+#endif
+#ifndef MMLTTB_STREAM_MIN_BLOCKS
+#define MMLTTB_STREAM_MIN_BLOCKS 1
+#endif
+constexpr int kUnroll = MMLTTB_STREAM_UNROLL;  // 16-byte vectors in flight per lane
 
 __device__ __forceinline__ float4 ld_stream4(const float4* p) {
   float4 v;
@@ -69,16 +76,18 @@ __device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesP
 // Warp-wide first-occurrence argmin/argmax of y[lo, hi) for float32 y.
 __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) {
   const uint32_t len = (uint32_t)(hi - lo);
-  const float v0 = __ldg(y + lo);  // every lane starts from the first point (offset 0)
-  float mn = v0, mx = v0;
-  uint32_t omn = 0, omx = 0;
+  const float inf = __int_as_float(0x7f800000);
+  // Empty state: only strictly smaller (larger) values are recorded, so a lane that
+  // sees nothing but +inf (-inf) keeps offset ~0u; if every lane does, the extreme is
+  // the first point (offset 0).
+  float mn = inf, mx = -inf;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
   const uintptr_t aend = ybase + (uintptr_t)hi * 4u;
   const int64_t nvec = (int64_t)((aend - a0 + 15u) >> 4);
   const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 4 - lo);  // in [-3, 0]
   const float4* vp = (const float4*)a0;
-  const float inf = __int_as_float(0x7f800000);
   for (int64_t v = lane; v < nvec; v += 32 * kUnroll) {
     float4 buf[kUnroll];
 #pragma unroll
@@ -122,8 +131,8 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) 
   Record r;
   r.kmin = wmn;
   r.kmax = wmx;
-  r.imin = lo + (int64_t)wo;
-  r.imax = lo + (int64_t)wx;
+  r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
+  r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
   return r;
 }
 
@@ -133,10 +142,11 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) 
 // are compared exactly through order-preserving int64 keys.
 __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane) {
   const uint32_t len = (uint32_t)(hi - lo);
-  const long long b0 = __double_as_longlong(__ldg(y + lo));
-  long long kmn = key64(__longlong_as_double(b0)), kmx = kmn;
-  float pmn = proxy_of_hi((unsigned)(b0 >> 32)), pmx = pmn;
-  uint32_t omn = 0, omx = 0;
+  // Empty state: keys beyond every double's key and NaN proxies, so the first
+  // element a lane sees takes the exact path and is recorded.
+  long long kmn = LLONG_MAX, kmx = LLONG_MIN;
+  float pmn = __int_as_float(0x7fc00000), pmx = pmn;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 8u) & ~(uintptr_t)15;
   const uintptr_t aend = ybase + (uintptr_t)hi * 8u;
@@ -190,8 +200,8 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane)
   Record r;
   r.kmin = ((long long)whm << 32) | wlm;
   r.kmax = ((long long)whx << 32) | wlx;
-  r.imin = lo + (int64_t)wo;
-  r.imax = lo + (int64_t)wx;
+  r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
+  r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
   return r;
 }
 
@@ -214,7 +224,7 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
   }
 }
 
-__global__ void __launch_bounds__(kStreamThreads) k_stream(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(kStreamThreads, MMLTTB_STREAM_MIN_BLOCKS) k_stream(const __grid_constant__ Batch bt) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
   if (w >= bt.n_warps) return;
