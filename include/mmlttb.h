@@ -46,6 +46,7 @@ extern "C" {
 #define MMLTTB_ERANGE (-6)   /* output capacity too small */
 #define MMLTTB_EDEVICE (-7)  /* a device-side check failed (status word) */
 #define MMLTTB_ENOMEM (-8)   /* host memory for a batch object could not be allocated */
+#define MMLTTB_ESCRATCH (-9) /* sizes need more than the static scratch of mmlttb_minmaxlttb_noalloc */
 
 /* Element type of y. */
 #define MMLTTB_F32 0
@@ -130,6 +131,31 @@ int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64
                       int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
                       int64_t out_cap, int64_t *out_count, void *workspace,
                       size_t workspace_bytes, mmlttb_stream stream);
+
+/*
+ * MinMaxLTTB without a workspace argument and without any allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need a result -- code running while a CUDA stream is
+ * being captured, latency-critical loops that forbid cudaMalloc/cudaFree because
+ * those can synchronize the whole device, and plugin hosts that offer no
+ * allocator.  Same arguments, semantics and results as mmlttb_minmaxlttb, minus
+ * the workspace pair; the caller still provides the inputs and out_idx/out_count.
+ *   Scratch: a 4 MiB array compiled into the library (a static __device__
+ *   variable), so every GPU that loads the library holds those 4 MiB until the
+ *   process exits.  Sizes whose workspace (mmlttb_workspace_bytes) exceeds 4 MiB
+ *   return MMLTTB_ESCRATCH and enqueue nothing; about 60 000 MinMax bins
+ *   (n_out * r_ps / 2) fit.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make that first
+ *   call before any stream capture begins.
+ *   Sharing: every call on a device uses the same array and leaves its contents
+ *   behind; each call clears what must start at zero.  Calls whose work overlaps on
+ *   the GPU (different streams, or different host threads) race on the array and
+ *   must be serialized by the caller.
+ */
+int mmlttb_minmaxlttb_noalloc(const void *y, int ydtype, const void *x, int xkind, int64_t n_in,
+                              int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
+                              int64_t out_cap, int64_t *out_count, mmlttb_stream stream);
 
 /*
  * MinMaxLTTB on HOST buffers, end to end (blocking).  Copies y (and x) from host

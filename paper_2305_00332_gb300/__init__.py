@@ -15,7 +15,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmmlttb.so")
 
-OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE, ENOMEM = 0, -1, -2, -3, -4, -6, -7, -8
+OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE, ENOMEM, ESCRATCH = 0, -1, -2, -3, -4, -6, -7, -8, -9
 F32, F64 = 0, 1
 X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1

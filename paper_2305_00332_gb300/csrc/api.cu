@@ -520,6 +520,7 @@ const char* mmlttb_strerror(int code) {
     case MMLTTB_ERANGE: return "output capacity too small";
     case MMLTTB_EDEVICE: return "device-side check failed";
     case MMLTTB_ENOMEM: return "host memory allocation failed";
+    case MMLTTB_ESCRATCH: return "sizes exceed the 4 MiB static scratch of mmlttb_minmaxlttb_noalloc";
     default: return "unknown error";
   }
 }
@@ -708,3 +709,64 @@ int mmlttb_workspace_status(const void* workspace, int* status, mmlttb_stream st
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- no-allocation variant
+// Some callers cannot allocate device memory at the moment they need a result: code
+// that runs while a CUDA stream is being captured (cudaMalloc is not allowed there),
+// latency-critical loops whose owners forbid allocation because cudaMalloc/cudaFree
+// can synchronize the whole device and stall unrelated streams, and plugin hosts
+// (a database function, a chart server extension) that hand out no allocator at all.
+// For them mmlttb_minmaxlttb_noalloc runs on a scratch array that is part of the
+// library image itself: every GPU that loads the library keeps these bytes reserved
+// until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// symbol g_noalloc_scratch is only a host-side stand-in, so the address is taken
+// once per device, with that device current, through cudaGetSymbolAddress.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= 64) return MMLTTB_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MMLTTB_OK;
+}
+
+}  // namespace
+
+extern "C" int mmlttb_minmaxlttb_noalloc(const void* y, int ydtype, const void* x, int xkind,
+                                         int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
+                                         int64_t* out_idx, int64_t out_cap, int64_t* out_count,
+                                         mmlttb_stream stream) {
+  int32_t branch;
+  int64_t bins;
+  int rc = classify(MMLTTB_OP_MINMAXLTTB, ydtype, xkind, n_in, n_out, r_ps, binmode, &branch, &bins);
+  if (rc) return rc;
+  DevInfo d;
+  rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(MMLTTB_OP_MINMAXLTTB, ydtype, xkind, n_in, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  if (p.total > kNoAllocScratchBytes) return MMLTTB_ESCRATCH;
+  void* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  // run_single clears the scratch header (status word, barrier counter, counts) on
+  // the stream before its first kernel; every other byte it reads is written first.
+  return run_single(MMLTTB_OP_MINMAXLTTB, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx,
+                    out_cap, out_count, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
+}
