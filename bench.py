@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="1e9-xwidth",
+                    choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving"],
+                    help="the headline (default) or one of the other measured workloads")
     return ap.parse_args()
 
 
@@ -178,6 +181,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
+    if args.workload != "1e9-xwidth":
+        import bench_workloads
+        bench_workloads.run(args)
+        return
 
     import torch
     torch.cuda.set_device(local)
@@ -249,6 +256,22 @@ def main():
     kern_avg = sum(kern_ms) / len(kern_ms)
     clk = clocks.summary(t_wall0, t_wall1)
 
+    # per-kernel breakdown of a step (events between the kernels), outside the timed loop
+    names = ["edges", "stream", "merge", "tables", "chain"]
+    st_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(30)]
+    for evs in st_ev:
+        for ev in evs:
+            ev.record(stream)
+    torch.cuda.synchronize(dev)
+    for evs in st_ev:
+        mm.set_stage_events(evs)
+        step()
+    torch.cuda.synchronize(dev)
+    stage_us = {}
+    for i, nm in enumerate(names):
+        v = sorted(evs[i].elapsed_time(evs[i + 1]) * 1e3 for evs in st_ev)
+        stage_us[nm] = round(v[len(v) // 2], 2)
+
     mm.minmaxlttb(y, N_OUT, R_PS, x=x, binmode="xwidth", out=out, workspace=work, sync=False)
     res = out.cpu().numpy().copy()
     status = mm.workspace_status(work)
@@ -288,8 +311,12 @@ def main():
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             el = float(tt.item())
         e2e_same = bool(np.array_equal(r.numpy(), res))
-        e2e = {"value": ws * n * E / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-               "d2h_bytes_per_step": 8 * N_OUT + 8, "steps": E, "matches_device_result": e2e_same}
+        # pinned inputs are read in place over NVLink-C2C: every y once (8 B/point) and
+        # x at about 7 x 32 probes per bin edge plus the preselected points
+        h2d = 8 * n + 8 * (N_OUT * R_PS // 2 + 1) * 7 * 32 + 16 * (N_OUT * R_PS + 2)
+        e2e = {"value": ws * n * E / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 * N_OUT + 8, "steps": E, "matches_device_result": e2e_same,
+               "mode": "zero-copy: pinned host x/y read in place by the kernels over NVLink-C2C"}
         del dbuf
 
     cpu = None
@@ -319,6 +346,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "stage_us_median": stage_us,
         "clocks": clk,
         "parity_vs_oracle": parity,
         "status_word": status,

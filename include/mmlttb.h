@@ -47,6 +47,7 @@ extern "C" {
 #define MMLTTB_EDEVICE (-7)  /* a device-side check failed (status word) */
 #define MMLTTB_ENOMEM (-8)   /* host memory for a batch object could not be allocated */
 #define MMLTTB_ESCRATCH (-9) /* sizes need more than the static scratch of mmlttb_minmaxlttb_noalloc */
+#define MMLTTB_EBUSY (-10)   /* server queue full: resubmit later */
 
 /* Element type of y. */
 #define MMLTTB_F32 0
@@ -66,6 +67,7 @@ extern "C" {
 #define MMLTTB_OP_PRESELECT 0
 #define MMLTTB_OP_LTTB 1
 #define MMLTTB_OP_MINMAXLTTB 2
+#define MMLTTB_OP_M4 3
 
 /* Opaque CUDA stream handle; binary-compatible with cudaStream_t. */
 typedef struct CUstream_st *mmlttb_stream;
@@ -101,6 +103,20 @@ int mmlttb_minmax_preselect(const void *y, int ydtype, const void *x, int xkind,
                             int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
                             int64_t out_cap, int64_t *out_count, void *workspace,
                             size_t workspace_bytes, mmlttb_stream stream);
+
+/*
+ * M4 (Sec. 2.2.1 and Table 1: per bin the vertical extrema and the first and last
+ * point).  B = floor(n_out/4) bins (n_out >= 4) over ALL points 0..n_in-1: index
+ * bins [floor(i n/B), floor((i+1) n/B)), or equal-width x bins as for MinMax.  Per
+ * non-empty bin, its first point, first argmin, first argmax and last point, in
+ * increasing order without repeats: at most 4B indices.
+ *   out_idx   device int64[out_cap], out_cap >= min(n_in, 4B).
+ *   out_count device int64 (nullable): receives the number of indices written.
+ *   workspace at least mmlttb_workspace_bytes(MMLTTB_OP_M4, ...) bytes.
+ */
+int mmlttb_m4(const void *y, int ydtype, const void *x, int xkind, int64_t n_in, int64_t n_out,
+              int binmode, int64_t *out_idx, int64_t out_cap, int64_t *out_count, void *workspace,
+              size_t workspace_bytes, mmlttb_stream stream);
 
 /*
  * LTTB (Largest-Triangle-Three-Buckets; Sec. 2.2.1 and Table 1 of the paper, after
@@ -143,7 +159,7 @@ int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64
  *   Scratch: a 4 MiB array compiled into the library (a static __device__
  *   variable), so every GPU that loads the library holds those 4 MiB until the
  *   process exits.  Sizes whose workspace (mmlttb_workspace_bytes) exceeds 4 MiB
- *   return MMLTTB_ESCRATCH and enqueue nothing; about 60 000 MinMax bins
+ *   return MMLTTB_ESCRATCH and enqueue nothing; about 38 000 MinMax bins
  *   (n_out * r_ps / 2) fit.
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress, with that device current) and caches it; make that first
@@ -158,10 +174,13 @@ int mmlttb_minmaxlttb_noalloc(const void *y, int ydtype, const void *x, int xkin
                               int64_t out_cap, int64_t *out_count, mmlttb_stream stream);
 
 /*
- * MinMaxLTTB on HOST buffers, end to end (blocking).  Copies y (and x) from host
- * memory into `device_buffer` (pinned host memory makes the copies asynchronous
- * DMA), runs mmlttb_minmaxlttb there, copies the indices and the count back to
- * out_host / out_count_host, and synchronizes `stream` before returning.
+ * MinMaxLTTB on HOST buffers, end to end (blocking).  Pinned or registered host
+ * memory (cudaHostAlloc / cudaHostRegister) is read in place by the kernels over
+ * the CPU-GPU link, so only what the path touches crosses it: every y value once,
+ * x only at the bin-edge probes and the preselected points.  This also serves
+ * series larger than device memory.  Pageable host memory is first copied into
+ * `device_buffer`.  The indices and the count are copied back to out_host /
+ * out_count_host and `stream` is synchronized before returning.
  *   device_buffer  device memory of at least mmlttb_host_buffer_bytes(...) bytes,
  *                  owned by the caller (holds the staged input, the output and the
  *                  workspace).
@@ -188,7 +207,7 @@ int mmlttb_minmaxlttb_host(const void *y_host, int ydtype, const void *x_host, i
 typedef struct mmlttb_series_desc {
   const void *y;      /* device: n_in float32/float64 values */
   const void *x;      /* device: n_in int64/float64 values, or NULL with MMLTTB_X_IMPLICIT */
-  int32_t op;         /* MMLTTB_OP_MINMAXLTTB, MMLTTB_OP_LTTB or MMLTTB_OP_PRESELECT */
+  int32_t op;         /* MMLTTB_OP_MINMAXLTTB, MMLTTB_OP_LTTB, MMLTTB_OP_PRESELECT or MMLTTB_OP_M4 */
   int32_t ydtype;     /* MMLTTB_F32 / MMLTTB_F64 */
   int32_t xkind;      /* MMLTTB_X_* */
   int32_t binmode;    /* MMLTTB_BINS_* */
@@ -218,6 +237,73 @@ int mmlttb_batch_run_graph(mmlttb_batch_t batch, void *workspace, size_t workspa
 int mmlttb_batch_destroy(mmlttb_batch_t batch);
 
 /*
+ * Zoom-window server (continuous batching).  A visualisation front end asks for
+ * MinMaxLTTB of windows [start, end) of series that stay resident on the device
+ * (the interactive zoom/pan use case of Sec. 1 and Sec. 2.1).  Requests are queued;
+ * a scheduler thread owned by the server forms batches first come, first served
+ * whenever one of `streams` slots is free, admitting requests while the batch's
+ * workspace fits the slot's budget, and runs each batch as one batched launch
+ * sequence on the slot's stream.  Requests that arrive while batches are on the
+ * GPU join the next batch, so batches overlap on the device.  Results are the
+ * same as a single mmlttb_minmaxlttb call on the window (indices are absolute in
+ * the resident series).  Device memory comes from a caller-owned pool; the server
+ * allocates pinned host buffers for results and plan uploads.
+ */
+typedef struct mmlttb_server_config {
+  int32_t streams;                    /* batches in flight at once (>= 1), one stream each */
+  int32_t reserved;                   /* set to 0 */
+  int64_t max_batch;                  /* requests per batch at most */
+  int64_t max_n_out;                  /* largest n_out a request may ask for */
+  int64_t max_pending;                /* queue capacity; beyond it submit returns MMLTTB_EBUSY */
+  int64_t workspace_bytes_per_stream; /* device workspace per batch: the admission budget */
+} mmlttb_server_config;
+
+typedef struct mmlttb_request {
+  int64_t series;     /* id returned by mmlttb_server_add_series */
+  int64_t start, end; /* window [start, end) of the resident series, 0 <= start < end <= n */
+  int64_t n_out;      /* 3 <= n_out <= max_n_out */
+  int32_t r_ps;       /* >= 2 */
+  int32_t binmode;    /* MMLTTB_BINS_* */
+} mmlttb_request;
+
+typedef struct mmlttb_server_stats {
+  int64_t submitted, completed, rejected, batches, gpu_launches;
+  double mean_batch;
+  double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;
+} mmlttb_server_stats;
+
+typedef struct mmlttb_server *mmlttb_server_t;
+
+/* Device pool bytes a configuration needs (workspace, outputs and counts per stream). */
+int mmlttb_server_pool_bytes(const mmlttb_server_config *cfg, size_t *bytes);
+/* Start a server on the current device over a caller-owned device pool. */
+int mmlttb_server_create(const mmlttb_server_config *cfg, void *device_pool, size_t pool_bytes,
+                         mmlttb_server_t *out);
+/* Register a resident series (device pointers, owned by the caller, kept valid
+   until the server is destroyed). */
+int mmlttb_server_add_series(mmlttb_server_t server, const void *y, int ydtype, const void *x,
+                             int xkind, int64_t n, int64_t *series_id);
+/* Queue a request (thread-safe, returns at once).  MMLTTB_EINVAL for a malformed
+   request, MMLTTB_ENOSPC when it cannot fit a slot's workspace even alone,
+   MMLTTB_EBUSY when the queue is full. */
+int mmlttb_server_submit(mmlttb_server_t server, const mmlttb_request *req, uint64_t *request_id);
+/* Block until the request completes; copy its indices (host int64[out_cap]) and
+   release it.  latency_s (nullable) receives completion minus submission time. */
+int mmlttb_server_wait(mmlttb_server_t server, uint64_t request_id, int64_t *out_host,
+                       int64_t out_cap, int64_t *count, double *latency_s);
+/* Block until every submitted request has completed. */
+int mmlttb_server_drain(mmlttb_server_t server);
+/* Trace replay: submit reqs[i] at t_offset_s[i] seconds after the call starts
+   (offsets non-decreasing); ids[i] receives the id (0 when rejected) and status[i]
+   (nullable) the submit result.  Returns after the last submission. */
+int mmlttb_server_replay(mmlttb_server_t server, const mmlttb_request *reqs,
+                         const double *t_offset_s, int64_t n, uint64_t *ids, int *status);
+int mmlttb_server_get_stats(mmlttb_server_t server, mmlttb_server_stats *stats);
+int mmlttb_server_reset_stats(mmlttb_server_t server);
+/* Finish queued work, stop the scheduler and release the server's host buffers. */
+int mmlttb_server_destroy(mmlttb_server_t server);
+
+/*
  * Profiling hook (per calling thread, one shot): the next call that runs MinMax
  * preselection records `start_event` on its stream just before the streaming
  * MinMax kernel and `stop_event` just after it, then forgets both.  The events
@@ -225,6 +311,15 @@ int mmlttb_batch_destroy(mmlttb_batch_t batch);
  * between them is that kernel's device time.
  */
 int mmlttb_set_timing_events(void *start_event, void *stop_event);
+
+/*
+ * Profiling hook (per calling thread, one shot): the next single-series call
+ * records events[0] on its stream before its first kernel and events[k] after its
+ * k-th kernel, for as many events as given (at most 16), then forgets them.  For
+ * MinMaxLTTB with x-width bins the kernels are: edge search, MinMax stream,
+ * compaction, LTTB tables, LTTB chain.
+ */
+int mmlttb_set_stage_events(void *const *events, int count);
 
 /* Number of kernels this library has launched from the calling thread so far. */
 unsigned long long mmlttb_launch_count(void);

@@ -52,6 +52,8 @@ def load(path=None):
     lib.mmo_lttb_positions.argtypes = [vp, cint, vp, cint, vp, i64, i64, vp]
     lib.mmo_lttb.restype = i64
     lib.mmo_lttb.argtypes = [vp, cint, vp, cint, i64, i64, vp]
+    lib.mmo_m4.restype = i64
+    lib.mmo_m4.argtypes = [vp, cint, vp, cint, i64, i64, cint, vp]
     lib.mmo_minmaxlttb.restype = i64
     lib.mmo_minmaxlttb.argtypes = [vp, cint, vp, cint, i64, i64, i32, cint, vp]
     return lib
@@ -129,6 +131,14 @@ class Oracle:
         out = np.empty(max(min(n_out, len(idx)), 1), np.int64)
         m = self._rc(self.lib.mmo_lttb_positions(y.ctypes.data, yd, xp, xk, idx.ctypes.data, len(idx),
                                                  n_out, out.ctypes.data), "lttb_positions")
+        return out[:m].copy()
+
+    def m4(self, y, n_out, x=None, binmode="index"):
+        y, yd = self._y(y)
+        x, xk, xp = self._x(x, len(y))
+        out = np.empty(max(4 * (n_out // 4), 1), np.int64)
+        m = self._rc(self.lib.mmo_m4(y.ctypes.data, yd, xp, xk, len(y), n_out, self._bm(binmode),
+                                     out.ctypes.data), "m4")
         return out[:m].copy()
 
     def minmaxlttb(self, y, n_out, r_ps=4, x=None, binmode="index"):

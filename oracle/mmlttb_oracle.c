@@ -47,6 +47,10 @@
  *   R14 When fewer than n_out points are preselected (x mode), all are returned.
  *   R15 When r_ps*n_out >= n, minmaxlttb is plain LTTB on all points; when
  *       n_out >= n it returns every index.
+ *   R16 M4 (Sec. 2.2.1, Table 1: the vertical extrema and the first and last point
+ *       of each bin): B = floor(n_out/4) bins over ALL points 0..n-1, index bins
+ *       [floor(i n/B), floor((i+1) n/B)), x-width bins as R3 but over all points;
+ *       per non-empty bin the sorted distinct {first, argmin, argmax, last}.
  */
 #include <math.h>
 #include <stdint.h>
@@ -281,4 +285,70 @@ int64_t mmo_minmaxlttb(const void *y, int ydt, const void *x, int xk, int64_t n,
     int64_t r = mmo_lttb_positions(y, ydt, x, xk, sel, m, n_out, out);
     free(sel);
     return r;
+}
+
+/*
+ * M4 (Sec. 2.2.1, Table 1; reading R16): per bin the first point, the first argmin,
+ * the first argmax and the last point, in increasing index order without repeats.
+ * out must hold 4B indices.  Returns the number written, or a negative error.
+ */
+int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t n_out,
+               int binmode, int64_t *out)
+{
+    int rc = check_common(y, ydt, x, xk, n);
+    if (rc) return rc;
+    if (n_out < 4) return MMO_EINVAL;
+    if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    const int64_t B = n_out / 4;
+    if (n == 0) return 0;
+
+    int64_t *first = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    int64_t *last = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    int64_t *imin = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    int64_t *imax = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
+    double *vmin = (double *)malloc(sizeof(double) * (size_t)B);
+    double *vmax = (double *)malloc(sizeof(double) * (size_t)B);
+    if (!first || !last || !imin || !imax || !vmin || !vmax) {
+        free(first); free(last); free(imin); free(imax); free(vmin); free(vmax);
+        return MMO_ENOMEM;
+    }
+    for (int64_t b = 0; b < B; b++) first[b] = -1;
+    const int64_t *xi = (const int64_t *)x;
+    int64_t x0 = 0, D = 0;
+    if (binmode == BINS_XWIDTH) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
+    /* start (index mode) or left edge (x mode) of bin b+1; past the last bin, a bound
+       above every int64 */
+#define NEXT_BOUND4(bb)                                                                 \
+    ((bb) + 1 >= B ? (__int128)INT64_MAX + 1                                            \
+     : binmode == BINS_INDEX ? (__int128)(((unsigned __int128)((bb) + 1) * (uint64_t)n) / (uint64_t)B) \
+     : (__int128)x0 + ((__int128)((bb) + 1) * (__int128)D) / (__int128)B)
+    int64_t b = 0;
+    __int128 next = NEXT_BOUND4(b);
+    for (int64_t p = 0; p < n; p++) {
+        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
+        while (next <= here) {
+            b++;
+            next = NEXT_BOUND4(b);
+        }
+        double v = y_at(y, ydt, p);
+        if (first[b] < 0) {
+            first[b] = p; last[b] = p; imin[b] = p; imax[b] = p; vmin[b] = v; vmax[b] = v;
+        } else {
+            last[b] = p;
+            if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }
+            if (v > vmax[b]) { vmax[b] = v; imax[b] = p; }
+        }
+    }
+#undef NEXT_BOUND4
+    int64_t m = 0;
+    for (b = 0; b < B; b++) {
+        if (first[b] < 0) continue;
+        int64_t c[4] = {first[b], imin[b] < imax[b] ? imin[b] : imax[b],
+                        imin[b] < imax[b] ? imax[b] : imin[b], last[b]};
+        for (int k = 0; k < 4; k++)
+            if (k == 0 || c[k] != c[k - 1]) out[m++] = c[k];
+    }
+    free(first); free(last); free(imin); free(imax); free(vmin); free(vmax);
+    return m;
 }

@@ -19,7 +19,7 @@ OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE, ENOMEM, ESCRATCH = 0, -1, 
 F32, F64 = 0, 1
 X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1
-OP_PRESELECT, OP_LTTB, OP_MINMAXLTTB = 0, 1, 2
+OP_PRESELECT, OP_LTTB, OP_MINMAXLTTB, OP_M4 = 0, 1, 2, 3
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -45,6 +45,8 @@ lib.mmlttb_lttb.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _vp, _i64, _vp, _v
 lib.mmlttb_minmaxlttb.restype = _int
 lib.mmlttb_minmaxlttb.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _i32, _int, _vp, _i64, _vp, _vp,
                                   _sz, _vp]
+lib.mmlttb_m4.restype = _int
+lib.mmlttb_m4.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _int, _vp, _i64, _vp, _vp, _sz, _vp]
 lib.mmlttb_workspace_status.restype = _int
 lib.mmlttb_workspace_status.argtypes = [_vp, ctypes.POINTER(_int), _vp]
 lib.mmlttb_host_buffer_bytes.restype = _int
@@ -55,6 +57,8 @@ lib.mmlttb_minmaxlttb_host.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _i32, _
 lib.mmlttb_set_timing_events.restype = _int
 lib.mmlttb_set_timing_events.argtypes = [_vp, _vp]
 lib.mmlttb_launch_count.restype = ctypes.c_ulonglong
+lib.mmlttb_set_stage_events.restype = _int
+lib.mmlttb_set_stage_events.argtypes = [ctypes.POINTER(_vp), _int]
 
 
 class MMLTTBError(RuntimeError):
@@ -153,6 +157,24 @@ def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, works
     return _finish(out, count, sync)
 
 
+def m4(y, n_out, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True):
+    """M4 (mmlttb_m4): per bin of floor(n_out/4) bins over all points, the first,
+    argmin, argmax and last index, sorted and without repeats."""
+    _check_inputs(y, x)
+    n = y.numel()
+    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode)
+    cap = min(n, 4 * (n_out // 4))
+    if out is None:
+        out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    count = torch.empty(1, dtype=torch.int64, device=y.device)
+    ws = _workspace(workspace_bytes(OP_M4, yd, xk, n, n_out, 4, bm), y.device, workspace)
+    _check(lib.mmlttb_m4(
+        y.data_ptr(), yd, x.data_ptr() if x is not None else None, xk, n, n_out, bm,
+        out.data_ptr(), out.numel(), count.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(),
+        _stream(y.device)), "mmlttb_m4")
+    return _finish(out, count, sync)
+
+
 def lttb(y, n_out, x=None, out=None, workspace=None, sync=True):
     """Plain LTTB on all points (mmlttb_lttb): min(n_out, n) int64 indices."""
     _check_inputs(y, x)
@@ -237,6 +259,13 @@ def set_timing_events(start, stop):
            "mmlttb_set_timing_events")
 
 
+def set_stage_events(events):
+    """Arm one-shot events between the kernels of the next call (recorded torch
+    events: index 0 before the first kernel, k after the k-th)."""
+    arr = (_vp * len(events))(*[e.cuda_event for e in events])
+    _check(lib.mmlttb_set_stage_events(arr, len(events)), "mmlttb_set_stage_events")
+
+
 def launch_count():
     """Kernels launched by the library from this thread so far."""
     return int(lib.mmlttb_launch_count())
@@ -260,7 +289,7 @@ lib.mmlttb_batch_run_graph.argtypes = [_vp, _vp, _sz, _vp]
 lib.mmlttb_batch_destroy.restype = _int
 lib.mmlttb_batch_destroy.argtypes = [_vp]
 
-_OPS = {"minmaxlttb": OP_MINMAXLTTB, "lttb": OP_LTTB, "preselect": OP_PRESELECT}
+_OPS = {"minmaxlttb": OP_MINMAXLTTB, "lttb": OP_LTTB, "preselect": OP_PRESELECT, "m4": OP_M4}
 
 
 class Batch:
@@ -283,7 +312,8 @@ class Batch:
             op = _OPS[s.get("op", "minmaxlttb")]
             r_ps = int(s.get("r_ps", 4))
             n, n_out = y.numel(), int(s["n_out"])
-            cap = min(n, (n_out * r_ps // 2) * 2 + 2) if op == OP_PRESELECT else min(n, n_out)
+            cap = (min(n, (n_out * r_ps // 2) * 2 + 2) if op == OP_PRESELECT
+                   else min(n, 4 * (n_out // 4)) if op == OP_M4 else min(n, n_out))
             caps.append(max(cap, 0))
             d = descs[i]
             d.y = y.data_ptr()
@@ -327,6 +357,128 @@ class Batch:
         if getattr(self, "_h", None):
             torch.cuda.synchronize(self.device)
             lib.mmlttb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+EBUSY = -10
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("streams", _i32), ("reserved", _i32), ("max_batch", _i64), ("max_n_out", _i64),
+                ("max_pending", _i64), ("workspace_bytes_per_stream", _i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("series", _i64), ("start", _i64), ("end", _i64), ("n_out", _i64), ("r_ps", _i32),
+                ("binmode", _i32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("rejected", _i64), ("batches", _i64),
+                ("gpu_launches", _i64), ("mean_batch", ctypes.c_double), ("latency_p50_s", ctypes.c_double),
+                ("latency_p99_s", ctypes.c_double), ("latency_max_s", ctypes.c_double),
+                ("latency_mean_s", ctypes.c_double)]
+
+
+lib.mmlttb_server_pool_bytes.restype = _int
+lib.mmlttb_server_pool_bytes.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_sz)]
+lib.mmlttb_server_create.restype = _int
+lib.mmlttb_server_create.argtypes = [ctypes.POINTER(ServerConfig), _vp, _sz, ctypes.POINTER(_vp)]
+lib.mmlttb_server_add_series.restype = _int
+lib.mmlttb_server_add_series.argtypes = [_vp, _vp, _int, _vp, _int, _i64, ctypes.POINTER(_i64)]
+lib.mmlttb_server_submit.restype = _int
+lib.mmlttb_server_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+lib.mmlttb_server_wait.restype = _int
+lib.mmlttb_server_wait.argtypes = [_vp, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64),
+                                   ctypes.POINTER(ctypes.c_double)]
+lib.mmlttb_server_drain.restype = _int
+lib.mmlttb_server_drain.argtypes = [_vp]
+lib.mmlttb_server_replay.restype = _int
+lib.mmlttb_server_replay.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double), _i64,
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_int)]
+lib.mmlttb_server_get_stats.restype = _int
+lib.mmlttb_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+lib.mmlttb_server_reset_stats.restype = _int
+lib.mmlttb_server_reset_stats.argtypes = [_vp]
+lib.mmlttb_server_destroy.restype = _int
+lib.mmlttb_server_destroy.argtypes = [_vp]
+
+
+class Server:
+    """Zoom-window MinMaxLTTB server with continuous batching (mmlttb_server_*).
+
+    Resident series are CUDA tensors the caller keeps alive; the device pool is a
+    torch allocation owned by this object."""
+
+    def __init__(self, streams=2, max_batch=256, max_n_out=4000, max_pending=1 << 20,
+                 workspace_bytes_per_stream=256 << 20, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.cfg = ServerConfig(streams, 0, max_batch, max_n_out, max_pending, workspace_bytes_per_stream)
+        nb = ctypes.c_size_t(0)
+        _check(lib.mmlttb_server_pool_bytes(ctypes.byref(self.cfg), ctypes.byref(nb)), "mmlttb_server_pool_bytes")
+        self.pool = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        h = _vp()
+        with torch.cuda.device(self.device):
+            _check(lib.mmlttb_server_create(ctypes.byref(self.cfg), self.pool.data_ptr(), nb.value,
+                                            ctypes.byref(h)), "mmlttb_server_create")
+        self._h = h
+        self._series = []
+
+    def add_series(self, y, x=None):
+        _check_inputs(y, x)
+        sid = _i64(0)
+        _check(lib.mmlttb_server_add_series(self._h, y.data_ptr(), _ydt(y), x.data_ptr() if x is not None else None,
+                                            _xkind(x), y.numel(), ctypes.byref(sid)), "mmlttb_server_add_series")
+        self._series.append((y, x))
+        return sid.value
+
+    def submit(self, series, start, end, n_out, r_ps=4, binmode=BINS_INDEX):
+        q = Request(series, start, end, n_out, r_ps, _binmode(binmode))
+        rid = ctypes.c_uint64(0)
+        rc = lib.mmlttb_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid))
+        if rc != OK:
+            raise MMLTTBError(rc, "mmlttb_server_submit")
+        return rid.value
+
+    def wait(self, rid):
+        import numpy as np
+        out = np.empty(self.cfg.max_n_out, dtype=np.int64)
+        cnt = _i64(0)
+        lat = ctypes.c_double(0.0)
+        _check(lib.mmlttb_server_wait(self._h, rid, out.ctypes.data, out.size, ctypes.byref(cnt), ctypes.byref(lat)),
+               "mmlttb_server_wait")
+        return out[: cnt.value].copy(), lat.value
+
+    def replay(self, requests, offsets_s):
+        n = len(requests)
+        arr = (Request * n)(*requests)
+        offs = (ctypes.c_double * n)(*offsets_s)
+        ids = (ctypes.c_uint64 * n)()
+        st = (_int * n)()
+        lib.mmlttb_server_replay(self._h, arr, offs, n, ids, st)
+        return list(ids), list(st)
+
+    def drain(self):
+        _check(lib.mmlttb_server_drain(self._h), "mmlttb_server_drain")
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib.mmlttb_server_get_stats(self._h, ctypes.byref(s)), "mmlttb_server_get_stats")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(lib.mmlttb_server_reset_stats(self._h), "mmlttb_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mmlttb_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -12,28 +12,27 @@
 #include <new>
 #include <vector>
 
-#include "common.cuh"
+#include "host.h"
 
-using namespace mmlttb;
+namespace mmlttb {
 
-namespace {
 
 thread_local int g_last_cuda_error = 0;
-thread_local unsigned long long g_launches = 0;   // kernels launched by this thread
+thread_local unsigned long long g_launches = 0;
 thread_local cudaEvent_t g_ev_start = nullptr;     // one-shot events around k_stream
 thread_local cudaEvent_t g_ev_stop = nullptr;
+thread_local cudaEvent_t g_stage_ev[16];            // one-shot events between the kernels
+thread_local int g_stage_n = 0, g_stage_i = 0;
+
+// Record the next armed stage event (if any) on `st`.
+void stage_mark(cudaStream_t st) {
+  if (g_stage_i < g_stage_n) cudaEventRecord(g_stage_ev[g_stage_i++], st);
+}
 
 int cuda_fail(cudaError_t e) {
   g_last_cuda_error = (int)e;
   return MMLTTB_ECUDA;
 }
-
-struct DevInfo {
-  int sms = 0;
-  int stream_bps = 0;
-  int grid_bps = 0;
-  bool ok = false;
-};
 
 std::mutex g_dev_mu;
 DevInfo g_dev[64];
@@ -58,28 +57,25 @@ int get_dev_info(DevInfo* out) {
   return MMLTTB_OK;
 }
 
-size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
-
-constexpr size_t kHeader = 256;  // status word @0, barrier counter @4, m @8
 
 struct SinglePlan {
   int32_t branch = BR_ARANGE, engine = EN_NONE;
   int64_t B = 0, K = 0, npos = 0, W = 0, Wcap = 0, tab_cap = 0;
   int grid_lttb = 0;
   size_t off_edges = 0, off_rec = 0, off_sel = 0, off_tab = 0, off_means = 0, off_partial = 0;
+  size_t off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, off_px = 0, off_py = 0;
+  int64_t nct = 0;  // compaction CTAs
+  int64_t nb = 0;   // binned points
   size_t total = kHeader;
 };
 
-// Largest LTTB bucket over m positions with K buckets: ceil((m-2)/K).
-int64_t max_bucket(int64_t m, int64_t K) { return (m - 2 + K - 1) / K; }
 
-// Host-only validation and branch choice (Sec. 3 dispatch); needs no device.
 int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
              int32_t* branch, int64_t* bins) {
   if (ydt != MMLTTB_F32 && ydt != MMLTTB_F64) return MMLTTB_EINVAL;
   if (xk != MMLTTB_X_IMPLICIT && xk != MMLTTB_X_I64 && xk != MMLTTB_X_F64) return MMLTTB_EINVAL;
   if (n < 0 || n_out < 0) return MMLTTB_EINVAL;
-  const bool uses_bins = op == MMLTTB_OP_PRESELECT || op == MMLTTB_OP_MINMAXLTTB;
+  const bool uses_bins = op == MMLTTB_OP_PRESELECT || op == MMLTTB_OP_MINMAXLTTB || op == MMLTTB_OP_M4;
   if (uses_bins) {
     if (binmode != MMLTTB_BINS_INDEX && binmode != MMLTTB_BINS_XWIDTH) return MMLTTB_EINVAL;
     if (binmode == MMLTTB_BINS_XWIDTH && xk != MMLTTB_X_I64) return MMLTTB_EINVAL;
@@ -93,6 +89,11 @@ int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, in
       B = n_out * (int64_t)r_ps / 2;
       if (B < 1) return MMLTTB_EINVAL;
       br = BR_PRESELECT;
+      break;
+    case MMLTTB_OP_M4:
+      if (n_out < 4) return MMLTTB_EINVAL;
+      B = n_out / 4;
+      br = BR_M4;
       break;
     case MMLTTB_OP_LTTB:
       if (n_out >= n) br = BR_ARANGE;
@@ -122,20 +123,37 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
   int rc = classify(op, ydt, xk, n, n_out, r_ps, binmode, &p.branch, &p.B);
   if (rc) return rc;
   size_t off = kHeader;
-  if (p.branch == BR_PRESELECT || p.branch == BR_MINMAX_LTTB) {
-    p.npos = n > 2 ? n - 2 : 0;
+  if (binned(p.branch)) {
+    const int64_t N = p.branch == BR_M4 ? n : (n > 2 ? n - 2 : 0);
+    p.nb = N;
+    p.npos = series_work(N, p.B);
     p.Wcap = (int64_t)d.sms * d.stream_bps * kStreamWarps;
-    p.W = p.npos < p.Wcap ? p.npos : p.Wcap;
-    if (p.W > 0 && p.npos / p.W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // per-warp span
+    p.W = p.npos / (kBinCost + 1);  // every warp gets at least one point
+    if (p.W > p.Wcap) p.W = p.Wcap;
+    if (p.W < 1 && p.npos > 0) p.W = 1;
+    if (p.W > 0 && N / p.W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // per-warp span
     if (binmode == MMLTTB_BINS_XWIDTH) {
       p.off_edges = off;
       off = align256(off + (size_t)(p.B + 1) * 8);
     }
     p.off_rec = off;
     off = align256(off + (size_t)(p.B + p.Wcap) * sizeof(Record));
+    p.nct = (p.B + kBinsPerCta - 1) / kBinsPerCta;
+    p.off_binres = off;
+    off = align256(off + (size_t)p.nct * kBinsPerCta * 16);
+    p.off_ctasum = off;
+    off = align256(off + (size_t)p.nct * 4);
+    p.off_ctaser = off;
+    off = align256(off + (size_t)p.nct * 4);
+    p.off_ctaoff = off;
+    off = align256(off + (size_t)p.nct * 8);
   }
   if (p.branch == BR_MINMAX_LTTB) {
     p.off_sel = off;
+    off = align256(off + (size_t)(2 * p.B + 2) * 8);
+    p.off_px = off;
+    off = align256(off + (size_t)(2 * p.B + 2) * 8);
+    p.off_py = off;
     off = align256(off + (size_t)(2 * p.B + 2) * 8);
   }
   if (p.branch == BR_LTTB_ALL || p.branch == BR_MINMAX_LTTB) {
@@ -169,6 +187,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   if (n > 0 && y == nullptr) return MMLTTB_EINVAL;
   if (xk != MMLTTB_X_IMPLICIT && n > 0 && x == nullptr) return MMLTTB_EINVAL;
   const int64_t need = branch == BR_PRESELECT ? (n < 2 * bins + 2 ? n : 2 * bins + 2)
+                       : branch == BR_M4      ? (n < 4 * bins ? n : 4 * bins)
                                               : (n_out < n ? n_out : n);
   if (need > 0 && out == nullptr) return MMLTTB_EINVAL;
   if (out_cap < need) return MMLTTB_ERANGE;
@@ -206,7 +225,13 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.tab_off = 0;
   sp.tab_cap = p.tab_cap;
   sp.m_ptr = (int64_t*)(w + 8);
-  sp.sel = p.branch == BR_PRESELECT ? out : (p.branch == BR_MINMAX_LTTB ? (int64_t*)(w + p.off_sel) : nullptr);
+  sp.p0 = p.branch == BR_M4 ? 0 : 1;
+  sp.nb = p.nb;
+  sp.sel = (p.branch == BR_PRESELECT || p.branch == BR_M4) ? out
+           : (p.branch == BR_MINMAX_LTTB ? (int64_t*)(w + p.off_sel) : nullptr);
+  sp.px = p.branch == BR_MINMAX_LTTB ? (double*)(w + p.off_px) : nullptr;
+  sp.py = p.branch == BR_MINMAX_LTTB ? (double*)(w + p.off_py) : nullptr;
+  sp.bincta_off = 0;
   sp.tab = p.engine == EN_TABLES ? (uint8_t*)(w + p.off_tab) : nullptr;
   sp.means = p.engine == EN_GRID ? (double*)(w + p.off_means) : nullptr;
   sp.out = out;
@@ -218,45 +243,72 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
   bt.edges = p.off_edges ? (int64_t*)(w + p.off_edges) : nullptr;
   bt.partial = p.off_partial ? (double*)(w + p.off_partial) : nullptr;
+  bt.total_bin_ctas = p.nct;
+  bt.binres = p.off_binres ? (int64_t*)(w + p.off_binres) : nullptr;
+  bt.cta_sum = p.off_ctasum ? (int32_t*)(w + p.off_ctasum) : nullptr;
+  bt.cta_series = p.off_ctaser ? (int32_t*)(w + p.off_ctaser) : nullptr;
+  bt.cta_off = p.off_ctaoff ? (int64_t*)(w + p.off_ctaoff) : nullptr;
 
   cudaError_t e = cudaMemsetAsync(ws, 0, kHeader, st);
   if (e != cudaSuccess) return cuda_fail(e);
+  struct StageReset {  // the stage events are one-shot: disarm when this call returns
+    ~StageReset() { g_stage_n = g_stage_i = 0; }
+  } stage_reset;
+  stage_mark(st);
   if (p.branch == BR_ARANGE) {
     e = launch_iota(out, n, out_count, st);
     if (e != cudaSuccess) return cuda_fail(e);
     ++g_launches;
     return MMLTTB_OK;
   }
-  if (p.branch == BR_PRESELECT || p.branch == BR_MINMAX_LTTB) {
+  if (binned(p.branch)) {
     if (bt.total_edges > 0) {
       if ((e = launch_edges(bt, st)) != cudaSuccess) return cuda_fail(e);
+      stage_mark(st);
       ++g_launches;
     }
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
       if ((e = launch_stream(bt, grid, st)) != cudaSuccess) return cuda_fail(e);
+      stage_mark(st);
       ++g_launches;
     }
     if (g_ev_stop && (e = cudaEventRecord(g_ev_stop, st)) != cudaSuccess) return cuda_fail(e);
     g_ev_start = g_ev_stop = nullptr;
-    if ((e = launch_merge(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
-    ++g_launches;
+    if ((e = launch_compact(bt, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
+    g_launches += 3;
   }
-  if (p.branch == BR_PRESELECT) return MMLTTB_OK;
+  if (p.branch == BR_PRESELECT || p.branch == BR_M4) return MMLTTB_OK;
   if (p.engine == EN_TABLES) {
     if ((e = launch_tables(bt, st)) != cudaSuccess) return cuda_fail(e);
-    if ((e = launch_chain(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
+    if ((e = launch_chain(bt, 1, p.tab_cap, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
     g_launches += 2;
   } else {
     if (p.branch == BR_MINMAX_LTTB) {
-      if ((e = launch_chain(bt, 1, st)) != cudaSuccess) return cuda_fail(e);
+      if ((e = launch_chain(bt, 1, 0, st)) != cudaSuccess) return cuda_fail(e);
       ++g_launches;
     }
     if ((e = launch_lttb_grid(bt, p.grid_lttb, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
   return MMLTTB_OK;
+}
+
+// Device address of host memory the GPU may read in place (pinned or registered;
+// with unified addressing it is the same address), or NULL.
+const void* host_device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+  return nullptr;
 }
 
 // Device staging layout of mmlttb_minmaxlttb_host: y | x | out | count | workspace.
@@ -297,216 +349,9 @@ int host_layout(int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int bin
 }
 
 
-// ---------------------------------------------------------------- batches
-// A batch plans many series once (host), lays them out in one caller-owned
-// workspace, uploads the plan table with one copy from pinned host memory, and runs
-// the same kernels as a single series over all of them: one MinMax stream over the
-// concatenated interior points, one merge CTA per series, one table pass over all
-// positions, one chain CTA per series.  The launch sequence can be captured into a
-// CUDA graph once and replayed.
-struct BatchImpl {
-  std::vector<mmlttb_series_desc> descs;
-  std::vector<SeriesPlan> plans;  // pointer fields filled per workspace address
-  int64_t n = 0;
-  int64_t total_pos = 0, total_bins = 0, total_edges = 0, total_slots = 0;
-  int64_t Wcap = 0, W = 0;
-  bool any_block = false;
-  size_t off_plans = 0, off_pos = 0, off_edge = 0, off_tab = 0, off_m = 0, off_edges = 0,
-         off_rec = 0, off_sel = 0, off_tabs = 0, off_means = 0, total = kHeader, upload_bytes = 0;
-  std::vector<int64_t> sel_off, tab_byte_off, mean_off;
-  char* pinned = nullptr;       // upload image: plans | pos_offs | edge_offs | tab_offs
-  const void* bound_ws = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  const void* graph_ws = nullptr;
-  cudaStream_t capture_stream = nullptr;
-  int graph_launches = 0;
-  ~BatchImpl() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (capture_stream) cudaStreamDestroy(capture_stream);
-    if (pinned) cudaFreeHost(pinned);
-  }
-};
+}  // namespace mmlttb
 
-int batch_plan(BatchImpl* b, const DevInfo& d) {
-  const int64_t n = b->n;
-  b->plans.assign(n, SeriesPlan{});
-  b->sel_off.assign(n, -1);
-  b->tab_byte_off.assign(n, -1);
-  b->mean_off.assign(n, -1);
-  int64_t pos = 0, bins = 0, edges = 0, slots = 0, sel = 0, means = 0;
-  for (int64_t s = 0; s < n; ++s) {
-    const mmlttb_series_desc& D = b->descs[s];
-    int32_t br;
-    int64_t B;
-    int rc = classify(D.op, D.ydtype, D.xkind, D.n_in, D.n_out, D.r_ps, D.binmode, &br, &B);
-    if (rc) return rc;
-    if (D.n_in > 0 && D.y == nullptr) return MMLTTB_EINVAL;
-    if (D.xkind != MMLTTB_X_IMPLICIT && D.n_in > 0 && D.x == nullptr) return MMLTTB_EINVAL;
-    const int64_t need = br == BR_PRESELECT ? (D.n_in < 2 * B + 2 ? D.n_in : 2 * B + 2)
-                                            : (D.n_out < D.n_in ? D.n_out : D.n_in);
-    if (need > 0 && D.out_idx == nullptr) return MMLTTB_EINVAL;
-    if (D.out_cap < need) return MMLTTB_ERANGE;
-    SeriesPlan& sp = b->plans[s];
-    sp.y = D.y;
-    sp.x = D.xkind == MMLTTB_X_IMPLICIT ? nullptr : D.x;
-    sp.ydt = D.ydtype;
-    sp.xk = D.xkind;
-    sp.binmode = D.binmode;
-    sp.branch = br;
-    sp.r_ps = D.r_ps;
-    sp.n = D.n_in;
-    sp.n_out = D.n_out;
-    sp.B = B;
-    sp.out = D.out_idx;
-    sp.out_count = D.out_count;
-    sp.bin_off = bins;
-    sp.pos_off = pos;
-    sp.edge_off = edges;
-    sp.tab_off = slots;
-    const bool mm = br == BR_PRESELECT || br == BR_MINMAX_LTTB;
-    if (mm) {
-      sp.npos = D.n_in > 2 ? D.n_in - 2 : 0;
-      pos += sp.npos;
-      bins += B;
-      if (D.binmode == MMLTTB_BINS_XWIDTH) edges += B + 1;
-    }
-    if (br == BR_MINMAX_LTTB) {
-      b->sel_off[s] = sel;
-      sel += 2 * B + 2;
-    }
-    if (br == BR_LTTB_ALL || br == BR_MINMAX_LTTB) {
-      const int64_t K = D.n_out - 2;
-      const int64_t mcap = br == BR_LTTB_ALL ? D.n_in : 2 * B + 2;
-      if (max_bucket(mcap, K) <= kTableMaxBucket) {
-        sp.engine = EN_TABLES;
-        sp.tab_cap = mcap;
-        b->tab_byte_off[s] = slots;
-        slots += mcap;
-      } else {
-        sp.engine = EN_BLOCK;
-        b->any_block = true;
-        b->mean_off[s] = means;
-        means += 2 * K;
-      }
-    }
-  }
-  b->total_pos = pos;
-  b->total_bins = bins;
-  b->total_edges = edges;
-  b->total_slots = slots;
-  b->Wcap = (int64_t)d.sms * d.stream_bps * kStreamWarps;
-  b->W = pos < b->Wcap ? pos : b->Wcap;
-  if (b->W > 0 && pos / b->W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;
-  size_t off = kHeader;
-  auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-  b->off_plans = take((size_t)n * sizeof(SeriesPlan));
-  b->off_pos = take((size_t)(n + 1) * 8);
-  b->off_edge = take((size_t)(n + 1) * 8);
-  b->off_tab = take((size_t)(n + 1) * 8);
-  b->upload_bytes = off - b->off_plans;
-  b->off_m = take((size_t)n * 8);
-  b->off_edges = take((size_t)edges * 8);
-  b->off_rec = take((size_t)(bins + b->Wcap) * sizeof(Record));
-  b->off_sel = take((size_t)sel * 8);
-  b->off_tabs = take((size_t)slots);
-  b->off_means = take((size_t)means * 8);
-  b->total = off;
-  cudaError_t e = cudaHostAlloc((void**)&b->pinned, b->upload_bytes, cudaHostAllocDefault);
-  if (e != cudaSuccess) return cuda_fail(e);
-  // the offset tables never depend on the workspace address
-  int64_t* po = (int64_t*)(b->pinned + (b->off_pos - b->off_plans));
-  int64_t* eo = (int64_t*)(b->pinned + (b->off_edge - b->off_plans));
-  int64_t* to = (int64_t*)(b->pinned + (b->off_tab - b->off_plans));
-  for (int64_t s = 0; s < n; ++s) {
-    po[s] = b->plans[s].pos_off;
-    eo[s] = b->plans[s].edge_off;
-    to[s] = b->plans[s].tab_off;
-  }
-  po[n] = pos;
-  eo[n] = edges;
-  to[n] = slots;
-  return MMLTTB_OK;
-}
-
-// Point every plan at its sections of workspace `ws` and refresh the upload image.
-void batch_bind(BatchImpl* b, void* ws) {
-  char* w = (char*)ws;
-  for (int64_t s = 0; s < b->n; ++s) {
-    SeriesPlan& sp = b->plans[s];
-    sp.m_ptr = (int64_t*)(w + b->off_m) + s;
-    sp.sel = sp.branch == BR_PRESELECT ? sp.out
-             : sp.branch == BR_MINMAX_LTTB ? (int64_t*)(w + b->off_sel) + b->sel_off[s] : nullptr;
-    sp.tab = sp.engine == EN_TABLES ? (uint8_t*)(w + b->off_tabs) + b->tab_byte_off[s] : nullptr;
-    sp.means = sp.engine == EN_BLOCK ? (double*)(w + b->off_means) + b->mean_off[s] : nullptr;
-  }
-  memcpy(b->pinned, b->plans.data(), (size_t)b->n * sizeof(SeriesPlan));
-  b->bound_ws = ws;
-}
-
-Batch batch_args(const BatchImpl* b, void* ws) {
-  char* w = (char*)ws;
-  Batch bt;
-  memset(&bt, 0, sizeof(bt));
-  bt.plans = (const SeriesPlan*)(w + b->off_plans);
-  bt.pos_offs = (const int64_t*)(w + b->off_pos);
-  bt.edge_offs = (const int64_t*)(w + b->off_edge);
-  bt.tab_offs = (const int64_t*)(w + b->off_tab);
-  bt.n_series = (int32_t)b->n;
-  bt.total_pos = b->total_pos;
-  bt.n_warps = b->W;
-  bt.total_edges = b->total_edges;
-  bt.total_slots = b->total_slots;
-  bt.rec = (Record*)(w + b->off_rec);
-  bt.edges = (int64_t*)(w + b->off_edges);
-  bt.status = (unsigned*)w;
-  bt.barrier = (unsigned*)(w + 4);
-  return bt;
-}
-
-// Enqueue the whole batch on `st`: upload, then the kernels (capturable).
-int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
-  if (b->bound_ws != ws) batch_bind(b, ws);
-  const Batch bt = batch_args(b, ws);
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(ws, 0, kHeader, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaMemcpyAsync((char*)ws + b->off_plans, b->pinned, b->upload_bytes,
-                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return cuda_fail(e);
-  const int nb = (int)b->n;
-  if (bt.total_edges > 0) {
-    if ((e = launch_edges(bt, st)) != cudaSuccess) return cuda_fail(e);
-    ++g_launches;
-  }
-  if (b->W > 0) {
-    const int64_t grid = (b->W + kStreamWarps - 1) / kStreamWarps;
-    if ((e = launch_stream(bt, grid, st)) != cudaSuccess) return cuda_fail(e);
-    if ((e = launch_merge(bt, nb, st)) != cudaSuccess) return cuda_fail(e);
-    g_launches += 2;
-  } else if (b->total_bins > 0 || b->total_pos == 0) {
-    // series with n <= 2 still need their trivial preselected list
-    if ((e = launch_merge(bt, nb, st)) != cudaSuccess) return cuda_fail(e);
-    ++g_launches;
-  }
-  if (bt.total_slots > 0) {
-    if ((e = launch_tables(bt, st)) != cudaSuccess) return cuda_fail(e);
-    ++g_launches;
-  }
-  if ((e = launch_chain(bt, nb, st)) != cudaSuccess) return cuda_fail(e);
-  ++g_launches;
-  if (b->any_block) {
-    if ((e = launch_lttb_block(bt, nb, st)) != cudaSuccess) return cuda_fail(e);
-    ++g_launches;
-  }
-  return MMLTTB_OK;
-}
-
-}  // namespace
-
-struct mmlttb_batch {
-  BatchImpl impl;
-};
+using namespace mmlttb;
 
 extern "C" {
 
@@ -521,6 +366,7 @@ const char* mmlttb_strerror(int code) {
     case MMLTTB_EDEVICE: return "device-side check failed";
     case MMLTTB_ENOMEM: return "host memory allocation failed";
     case MMLTTB_ESCRATCH: return "sizes exceed the 4 MiB static scratch of mmlttb_minmaxlttb_noalloc";
+    case MMLTTB_EBUSY: return "server queue full";
     default: return "unknown error";
   }
 }
@@ -552,6 +398,13 @@ int mmlttb_minmax_preselect(const void* y, int ydtype, const void* x, int xkind,
                             size_t workspace_bytes, mmlttb_stream stream) {
   return run_single(MMLTTB_OP_PRESELECT, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx,
                     out_cap, out_count, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int mmlttb_m4(const void* y, int ydtype, const void* x, int xkind, int64_t n_in, int64_t n_out,
+              int binmode, int64_t* out_idx, int64_t out_cap, int64_t* out_count, void* workspace,
+              size_t workspace_bytes, mmlttb_stream stream) {
+  return run_single(MMLTTB_OP_M4, y, ydtype, x, xkind, n_in, n_out, 4, binmode, out_idx, out_cap,
+                    out_count, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
 int mmlttb_lttb(const void* y, int ydtype, const void* x, int xkind, int64_t n_in, int64_t n_out,
@@ -596,14 +449,24 @@ int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, i
   char* b = (char*)device_buffer;
   const size_t es = ydtype == MMLTTB_F32 ? 4 : 8;
   cudaError_t e;
-  if (n_in > 0 && (e = cudaMemcpyAsync(b + l.y, y_host, (size_t)n_in * es, cudaMemcpyHostToDevice, st)))
-    return cuda_fail(e);
-  if (xkind != MMLTTB_X_IMPLICIT && n_in > 0 &&
-      (e = cudaMemcpyAsync(b + l.x, x_host, (size_t)n_in * 8, cudaMemcpyHostToDevice, st)))
-    return cuda_fail(e);
-  rc = run_single(MMLTTB_OP_MINMAXLTTB, b + l.y, ydtype, xkind == MMLTTB_X_IMPLICIT ? nullptr : b + l.x,
-                  xkind, n_in, n_out, r_ps, binmode, (int64_t*)(b + l.out), out_cap < need ? out_cap : need,
-                  (int64_t*)(b + l.count), b + l.ws, l.ws_bytes, st);
+  // Pinned or registered host memory is read in place by the kernels (over the
+  // CPU-GPU link): only the bytes the path touches cross it, i.e. every y once and x
+  // only at bin-edge probes and preselected points.  Pageable memory is staged.
+  const void* yd = host_device_view(y_host);
+  const void* xd = xkind == MMLTTB_X_IMPLICIT ? nullptr : host_device_view(x_host);
+  if (n_in > 0 && (!yd || (xkind != MMLTTB_X_IMPLICIT && !xd))) {
+    if ((e = cudaMemcpyAsync(b + l.y, y_host, (size_t)n_in * es, cudaMemcpyHostToDevice, st)))
+      return cuda_fail(e);
+    yd = b + l.y;
+    if (xkind != MMLTTB_X_IMPLICIT) {
+      if ((e = cudaMemcpyAsync(b + l.x, x_host, (size_t)n_in * 8, cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e);
+      xd = b + l.x;
+    }
+  }
+  rc = run_single(MMLTTB_OP_MINMAXLTTB, yd, ydtype, xd, xkind, n_in, n_out, r_ps, binmode,
+                  (int64_t*)(b + l.out), out_cap < need ? out_cap : need, (int64_t*)(b + l.count),
+                  b + l.ws, l.ws_bytes, st);
   if (rc) return rc;
   if (need > 0 && (e = cudaMemcpyAsync(out_host, b + l.out, (size_t)need * 8, cudaMemcpyDeviceToHost, st)))
     return cuda_fail(e);
@@ -614,77 +477,12 @@ int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, i
 }
 
 
-int mmlttb_batch_create(const mmlttb_series_desc* descs, int64_t n_series, mmlttb_batch_t* out) {
-  if (!out || n_series < 1 || n_series > INT32_MAX || !descs) return MMLTTB_EINVAL;
-  *out = nullptr;
-  DevInfo d;
-  int rc = get_dev_info(&d);
-  if (rc) return rc;
-  mmlttb_batch* b = new (std::nothrow) mmlttb_batch;
-  if (!b) return MMLTTB_ENOMEM;
-  b->impl.n = n_series;
-  b->impl.descs.assign(descs, descs + n_series);
-  rc = batch_plan(&b->impl, d);
-  if (rc) {
-    delete b;
-    return rc;
-  }
-  *out = b;
-  return MMLTTB_OK;
-}
 
-int mmlttb_batch_workspace_bytes(mmlttb_batch_t batch, size_t* bytes) {
-  if (!batch || !bytes) return MMLTTB_EINVAL;
-  *bytes = batch->impl.total;
-  return MMLTTB_OK;
-}
-
-int mmlttb_batch_run(mmlttb_batch_t batch, void* workspace, size_t workspace_bytes,
-                     mmlttb_stream stream) {
-  if (!batch) return MMLTTB_EINVAL;
-  if (!workspace || workspace_bytes < batch->impl.total) return MMLTTB_ENOSPC;
-  return batch_enqueue(&batch->impl, workspace, (cudaStream_t)stream);
-}
-
-int mmlttb_batch_run_graph(mmlttb_batch_t batch, void* workspace, size_t workspace_bytes,
-                           mmlttb_stream stream) {
-  if (!batch) return MMLTTB_EINVAL;
-  if (!workspace || workspace_bytes < batch->impl.total) return MMLTTB_ENOSPC;
-  BatchImpl& b = batch->impl;
-  cudaError_t e;
-  if (!b.exec || b.graph_ws != workspace) {
-    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
-    if (b.graph) { cudaGraphDestroy(b.graph); b.graph = nullptr; }
-    if (!b.capture_stream &&
-        (e = cudaStreamCreateWithFlags(&b.capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
-      return cuda_fail(e);
-    if ((e = cudaStreamBeginCapture(b.capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-      return cuda_fail(e);
-    const unsigned long long before = g_launches;
-    int rc = batch_enqueue(&b, workspace, b.capture_stream);
-    g_launches = before;  // captured, not launched
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(b.capture_stream, &g);
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    if (e != cudaSuccess) return cuda_fail(e);
-    b.graph = g;
-    if ((e = cudaGraphInstantiate(&b.exec, b.graph, 0)) != cudaSuccess) return cuda_fail(e);
-    b.graph_ws = workspace;
-    b.graph_launches = 0;
-    for (auto k : {b.total_edges > 0, b.W > 0, b.W > 0 || b.total_bins > 0 || b.total_pos == 0,
-                   b.total_slots > 0, true, b.any_block})
-      b.graph_launches += k ? 1 : 0;
-  }
-  if ((e = cudaGraphLaunch(b.exec, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
-  g_launches += b.graph_launches;
-  return MMLTTB_OK;
-}
-
-int mmlttb_batch_destroy(mmlttb_batch_t batch) {
-  delete batch;
+int mmlttb_set_stage_events(void* const* events, int count) {
+  if (count < 0 || count > 16 || (count > 0 && !events)) return MMLTTB_EINVAL;
+  for (int i = 0; i < count; ++i) g_stage_ev[i] = (cudaEvent_t)events[i];
+  g_stage_n = count;
+  g_stage_i = 0;
   return MMLTTB_OK;
 }
 

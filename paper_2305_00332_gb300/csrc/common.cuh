@@ -20,6 +20,7 @@ enum Branch : int32_t {
   BR_LTTB_ALL = 1,     // LTTB on all n points (plain LTTB, or r_ps*n_out >= n)
   BR_MINMAX_LTTB = 2,  // MinMax preselection, then LTTB on the preselected points
   BR_PRESELECT = 3,    // MinMax preselection only; the list goes to the output
+  BR_M4 = 4,           // M4: first, argmin, argmax, last of each bin over all points
 };
 
 // Which LTTB engine resolves the serial bucket chain.
@@ -32,6 +33,8 @@ enum Engine : int32_t {
 
 // Largest LTTB bucket (in points) the transition-table engine accepts.
 constexpr int kTableMaxBucket = 32;
+// Bins per CTA of the compaction kernels; every series' bins start on a CTA boundary.
+constexpr int kBinsPerCta = 256;
 // Threads of the streaming MinMax kernel's CTAs.
 constexpr int kStreamThreads = 256;
 constexpr int kStreamWarps = kStreamThreads / 32;
@@ -49,13 +52,18 @@ struct SeriesPlan {
   int32_t ydt, xk, binmode, branch, engine, r_ps;
   int64_t n, n_out;
   int64_t B;         // MinMax bins (minmax branches), else 0
+  int64_t p0;        // first binned point: 1 (MinMax over the interior) or 0 (M4)
+  int64_t nb;        // binned points: n-2 (MinMax) or n (M4)
   int64_t bin_off;   // global index of this series' bin 0 in the record space
   int64_t edge_off;  // index of this series' S_0 in the edge array (x-width bins)
-  int64_t pos_off;   // global interior position of point 1
-  int64_t npos;      // interior points in the global position space (n-2 or 0)
+  int64_t pos_off;   // offset of this series in the global work (cost) space
+  int64_t npos;      // its extent there: D = N + kBinCost*min(B, N) for N = n-2 > 0, else 0
   int64_t tab_off;   // first slot of this series in the table-slot space
   int64_t tab_cap;   // slots reserved (positions that may need a table entry)
+  int64_t bincta_off; // first compaction CTA of this series (minmax branches)
   int64_t* sel;      // preselected list (capacity 2B+2), NULL for BR_LTTB_ALL
+  double* px;        // x of each preselected position as FP64 (BR_MINMAX_LTTB), else NULL
+  double* py;        // y of each preselected position as FP64 (BR_MINMAX_LTTB), else NULL
   int64_t* m_ptr;    // number of preselected points (device), minmax branches
   uint8_t* tab;      // one transition-table byte per position (EN_TABLES)
   double* means;     // 2*K doubles: next-bucket means (EN_GRID / EN_BLOCK)
@@ -66,19 +74,26 @@ struct SeriesPlan {
 struct Batch {
   const SeriesPlan* plans;  // device array of n_series plans; NULL: the single plan `one`
   SeriesPlan one;
-  const int64_t* pos_offs;   // n_series+1 prefix of npos (NULL for a single series)
+  const int64_t* pos_offs;   // n_series+1 prefix of npos, the work space (NULL for a single series)
   const int64_t* edge_offs;  // n_series+1 prefix of edge counts
   const int64_t* tab_offs;   // n_series+1 prefix of tab_cap
+  const int64_t* cta_offs;   // n_series+1 prefix of compaction CTAs
   int32_t n_series;
-  int64_t total_pos;   // sum of npos
+  int64_t total_pos;   // sum of npos: the total work the streaming warps split evenly
   int64_t n_warps;     // streaming warps, each with at least one interior point
   int64_t total_edges; // sum over x-width series of B+1
   int64_t total_slots; // sum of tab_cap
+  int64_t total_bin_ctas;  // compaction CTAs over all minmax series
   Record* rec;         // total bins + n_warps records
   int64_t* edges;      // bin starts S_b of x-width series
+  int64_t* binres;     // per padded bin: (first argmin/argmax lower, higher) or (-1, -1)
+  int32_t* cta_sum;    // per compaction CTA: number of indices its bins emit
+  int32_t* cta_series; // per compaction CTA: its series
+  int64_t* cta_off;    // per compaction CTA: exclusive prefix of cta_sum within its series
   unsigned* status;    // error bits (1: a bounded wait timed out, 2: device check failed)
   unsigned* barrier;   // grid barrier counter (EN_GRID)
   double* partial;     // 2 x grid x (area, position) partials (EN_GRID)
+  int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
 };
 
 __host__ __device__ inline const SeriesPlan& plan_of(const Batch& bt, int s) {
@@ -109,6 +124,25 @@ __host__ __device__ inline int64_t muldiv(int64_t a, int64_t b, int64_t c) {
 #endif
 }
 
+// ceil(a*b/c) for a, b >= 0, c > 0 (exact, 128-bit intermediate when needed).
+__host__ __device__ inline int64_t muldiv_ceil(int64_t a, int64_t b, int64_t c) {
+#ifdef __CUDA_ARCH__
+  unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  unsigned long long hi = __umul64hi((unsigned long long)a, (unsigned long long)b);
+  if (hi == 0) {
+    const unsigned long long q = lo / (unsigned long long)c;
+    return (int64_t)(q + (q * (unsigned long long)c != lo ? 1 : 0));
+  }
+  const unsigned __int128 num = ((unsigned __int128)hi << 64) | lo;
+  const unsigned __int128 q = num / (unsigned long long)c;
+  return (int64_t)(q + (q * (unsigned long long)c != num ? 1 : 0));
+#else
+  const unsigned __int128 num = (unsigned __int128)(uint64_t)a * (uint64_t)b;
+  const unsigned __int128 q = num / (uint64_t)c;
+  return (int64_t)(q + (q * (uint64_t)c != num ? 1 : 0));
+#endif
+}
+
 // Start of part j when `items` items are split into `parts` equal-count parts,
 // counting from 1: floor(j*items/parts)+1.  Used for MinMax index bins over the
 // interior points and for LTTB buckets over the interior positions.
@@ -131,11 +165,22 @@ __host__ __device__ inline int64_t part_of(int64_t p, int64_t items, int64_t par
 #endif
 }
 
-// Streaming warp w covers global interior positions [floor(w*T/W), floor((w+1)*T/W)).
+// Work balance of the MinMax stream.  A bin costs about as much as kBinCost points
+// (its flush is a warp reduction and a record store), so every series occupies
+// D = N + kBinCost*min(B, N) units of a global work space in which interior point q
+// (0-based, q = p-1) sits at unit floor(q*D/N): strictly increasing, steps of at
+// most kBinCost+1.  Warps split the work space evenly, so a warp covering short
+// series with small bins gets fewer points.
+constexpr int64_t kBinCost = 64;
+__host__ __device__ inline int64_t series_work(int64_t N, int64_t B) {
+  return N > 0 ? N + kBinCost * (B < N ? B : N) : 0;
+}
+
+// Streaming warp w covers global work units [floor(w*T/W), floor((w+1)*T/W)).
 __host__ __device__ inline int64_t warp_begin(int64_t w, int64_t total, int64_t warps) {
   return muldiv(w, total, warps);
 }
-// The warp whose range holds global position g: floor(((g+1)*W - 1) / T).
+// The warp whose range holds global work unit g: floor(((g+1)*W - 1) / T).
 __host__ __device__ inline int64_t warp_of(int64_t g, int64_t total, int64_t warps) {
   return part_of(g + 1, total, warps);
 }
@@ -150,8 +195,19 @@ __device__ __forceinline__ long long key64(double v) {
   return s >= 0 ? s : -(s & 0x7fffffffffffffffLL);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor drains; it waits here (before it
+// reads anything the predecessor wrote) and lets its own successor launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
   if (status) atomicOr(status, bit);
+}
+
+// Branches that run the MinMax stream and the compaction.
+__host__ __device__ inline bool binned(int32_t branch) {
+  return branch == BR_MINMAX_LTTB || branch == BR_PRESELECT || branch == BR_M4;
 }
 
 // Coordinates of original point i as FP64 (implicit x is the index).
@@ -168,6 +224,18 @@ __device__ __forceinline__ double y_of(const SeriesPlan& sp, int64_t i) {
 __device__ __forceinline__ int64_t index_of(const SeriesPlan& sp, int64_t p) {
   return sp.sel ? sp.sel[p] : p;
 }
+// Coordinates of LTTB position p: the compacted copies after preselection, else the
+// original point p.
+__device__ __forceinline__ void pos_xy(const SeriesPlan& sp, int64_t p, double* x, double* y) {
+  if (sp.px) {
+    *x = sp.px[p];
+    *y = sp.py[p];
+  } else {
+    const int64_t i = index_of(sp, p);
+    *x = x_of(sp, i);
+    *y = y_of(sp, i);
+  }
+}
 
 // LTTB triangle area (Sec. 2.2.1): |(xa-xc)(yb-ya) - (xa-xb)(yc-ya)|, every
 // operation rounded on its own (no contraction into FMA).
@@ -179,11 +247,28 @@ __device__ __forceinline__ double tri_area(double xa, double ya, double xb, doub
 }
 
 // ---- host launchers (defined in minmax.cu / lttb.cu) ----
+// Launch `kernel(bt)` with programmatic stream serialization allowed.
+template <typename K>
+inline cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              const Batch& bt) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, bt);
+}
 cudaError_t launch_edges(const Batch& bt, cudaStream_t st);
 cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st);
-cudaError_t launch_merge(const Batch& bt, int n_blocks, cudaStream_t st);
+// Compaction (A-2): per-bin resolve, per-series scan of CTA totals, placement.
+cudaError_t launch_compact(const Batch& bt, cudaStream_t st);
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st);
-cudaError_t launch_chain(const Batch& bt, int n_blocks, cudaStream_t st);
+cudaError_t launch_chain(const Batch& bt, int n_blocks, int64_t max_positions, cudaStream_t st);
 cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_t st);
 cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st);
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st);

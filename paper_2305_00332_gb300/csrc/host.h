@@ -1,0 +1,79 @@
+// Host-side internals shared by the C ABI translation units (not part of the ABI).
+#pragma once
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mmlttb {
+
+extern thread_local int g_last_cuda_error;
+extern thread_local unsigned long long g_launches;  // kernels launched by this thread
+
+// Record the next armed per-stage profiling event (if any) on `st`.
+void stage_mark(cudaStream_t st);
+// Remember `e` as the thread's last CUDA error and return MMLTTB_ECUDA.
+int cuda_fail(cudaError_t e);
+
+struct DevInfo {
+  int sms = 0;
+  int stream_bps = 0;
+  int grid_bps = 0;
+  bool ok = false;
+};
+// SM count and kernel occupancies of the current device (cached per device).
+int get_dev_info(DevInfo* out);
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr size_t kHeader = 256;  // workspace header: status word @0, barrier counter @4, m @8
+
+// Largest LTTB bucket over m positions with K buckets: ceil((m-2)/K).
+inline int64_t max_bucket(int64_t m, int64_t K) { return (m - 2 + K - 1) / K; }
+
+// Host-only validation and branch choice (Sec. 3 dispatch); needs no device.
+int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
+             int32_t* branch, int64_t* bins);
+
+struct BatchImpl {
+  std::vector<mmlttb_series_desc> descs;
+  std::vector<SeriesPlan> plans;  // pointer fields filled per workspace address
+  int64_t n = 0;
+  int64_t total_pos = 0, total_bins = 0, total_edges = 0, total_slots = 0;
+  int64_t Wcap = 0, W = 0;
+  bool any_block = false;
+  int64_t max_tab = 0;  // largest per-series table storage (positions)
+  int64_t total_bin_ctas = 0;
+  size_t off_plans = 0, off_pos = 0, off_edge = 0, off_tab = 0, off_cta = 0, off_m = 0, off_edges = 0,
+         off_rec = 0, off_sel = 0, off_px = 0, off_py = 0, off_tabs = 0, off_means = 0,
+         off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, total = kHeader,
+         upload_bytes = 0;
+  std::vector<int64_t> sel_off, tab_byte_off, mean_off;
+  char* pinned = nullptr;       // upload image: plans | pos_offs | edge_offs | tab_offs | cta_offs
+  bool own_pinned = true;       // false: the image lives in a buffer lent by the caller
+  const void* bound_ws = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* graph_ws = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int graph_launches = 0;
+  ~BatchImpl() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (pinned && own_pinned) cudaFreeHost(pinned);
+  }
+};
+
+// Plan every series of b->descs (validation, branches, engines, workspace layout)
+// and fill the offset tables of the upload image.  `lend`, when not NULL, is a
+// pinned buffer of `lend_bytes` the image may use instead of its own allocation.
+int batch_plan(BatchImpl* b, const DevInfo& d, char* lend = nullptr, size_t lend_bytes = 0);
+// Bytes of the upload image batch_plan needs for n series.
+size_t batch_upload_bytes(int64_t n);
+// Point every plan at its sections of workspace `ws` and refresh the upload image.
+void batch_bind(BatchImpl* b, void* ws);
+// Enqueue the whole batch on `st`: header clear, upload, kernels (capturable).
+int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st);
+
+}  // namespace mmlttb

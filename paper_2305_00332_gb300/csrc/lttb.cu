@@ -21,6 +21,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kChainThreads = 512;
+constexpr int64_t kChainSmemMax = 160 * 1024;  // tables staged in shared memory up to this size
 
 __device__ __forceinline__ int64_t lttb_m(const SeriesPlan& sp) {
   return sp.branch == BR_LTTB_ALL ? sp.n : *sp.m_ptr;
@@ -37,9 +38,10 @@ __device__ void bucket_mean(const SeriesPlan& sp, int64_t lo, int64_t hi, double
     for (int64_t p = lo; p < hi; ++p) sy = __dadd_rn(sy, y_of(sp, p));
   } else {
     for (int64_t p = lo; p < hi; ++p) {
-      const int64_t i = index_of(sp, p);
-      sx = __dadd_rn(sx, x_of(sp, i));
-      sy = __dadd_rn(sy, y_of(sp, i));
+      double xp, yp;
+      pos_xy(sp, p, &xp, &yp);
+      sx = __dadd_rn(sx, xp);
+      sy = __dadd_rn(sy, yp);
     }
   }
   const double cnt = (double)(hi - lo);
@@ -59,42 +61,102 @@ __device__ __forceinline__ void next_bucket(int64_t j, int64_t K, int64_t N, int
   }
 }
 
-__global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Batch bt) {
+constexpr int kTableThreads = 64;  // small CTAs: the positions spread over every SM
+
+__global__ void __launch_bounds__(kTableThreads) k_tables(const __grid_constant__ Batch bt) {
+  pdl_wait();
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= bt.total_slots) return;
-  const int s = bt.tab_offs ? upper_index(bt.tab_offs, bt.n_series, slot) : 0;
-  const SeriesPlan& sp = plan_of(bt, s);
-  if (sp.engine != EN_TABLES) return;
-  const int64_t p = slot - sp.tab_off;
-  const int64_t m = lttb_m(sp);
-  if (p >= m || m <= sp.n_out) return;
-  const int64_t K = sp.n_out - 2, N = m - 2;
-  int64_t jt;  // the bucket whose pick follows a pick at position p
-  if (p == 0) jt = 0;
-  else if (p <= m - 2) jt = part_of(p, N, K) + 1;
-  else return;
-  if (jt >= K) return;
-  const int64_t lo = part_start(jt, N, K), hi = part_start(jt + 1, N, K);
-  int64_t nlo, nhi;
-  next_bucket(jt, K, N, m, &nlo, &nhi);
-  double xc, yc;
-  bucket_mean(sp, nlo, nhi, &xc, &yc);
-  const int64_t ia = index_of(sp, p);
-  const double xa = x_of(sp, ia), ya = y_of(sp, ia);
+  // Every lane stays to the warp-wide steps below; `work` marks lanes with a table
+  // entry to fill.
+  bool work = slot < bt.total_slots;
+  int s = 0;
+  int64_t p = 0, m = 0, K = 0, N = 0, jt = 0;
+  const SeriesPlan* spp = nullptr;
+  if (work) {
+    s = bt.tab_offs ? upper_index(bt.tab_offs, bt.n_series, slot) : 0;
+    spp = &plan_of(bt, s);
+    p = slot - spp->tab_off;
+    work = spp->engine == EN_TABLES;
+    if (work) {
+      m = lttb_m(*spp);
+      work = p < m && m > spp->n_out;
+    }
+    if (work) {
+      K = spp->n_out - 2;
+      N = m - 2;
+      if (p == 0) jt = 0;               // the bucket whose pick follows a pick at p
+      else if (p <= m - 2) jt = part_of(p, N, K) + 1;
+      else work = false;
+      if (jt >= K) work = false;
+    }
+  }
+  // Lanes that target the same bucket of the same series share its next-bucket mean:
+  // the lowest such lane computes it (R7) and broadcasts it.
+  const unsigned long long key = work ? ((unsigned long long)s << 40) ^ (unsigned long long)jt
+                                      : ~0ull - (unsigned long long)lane;
+  const unsigned group = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(group) - 1;
+  double xc = 0.0, yc = 0.0;
+  int64_t lo = 0, hi = 0;
+  if (work) {
+    const SeriesPlan& sp = *spp;
+    lo = part_start(jt, N, K);
+    hi = part_start(jt + 1, N, K);
+    if (lane == leader) {
+      int64_t nlo, nhi;
+      next_bucket(jt, K, N, m, &nlo, &nhi);
+      bucket_mean(sp, nlo, nhi, &xc, &yc);
+    }
+  }
+  xc = __shfl_sync(0xffffffffu, xc, leader);
+  yc = __shfl_sync(0xffffffffu, yc, leader);
+  if (!work) return;
+  const SeriesPlan& sp = *spp;
+  double xa, ya;
+  pos_xy(sp, p, &xa, &ya);
   long long best = -1;  // bits of a non-negative double order like the double
   int pick = 0;
   for (int64_t q = lo; q < hi; ++q) {
-    const int64_t ib = index_of(sp, q);
-    const double area = tri_area(xa, ya, x_of(sp, ib), y_of(sp, ib), xc, yc);
+    double xb, yb;
+    pos_xy(sp, q, &xb, &yb);
+    const double area = tri_area(xa, ya, xb, yb, xc, yc);
     const long long ab = __double_as_longlong(area);
     if (q == lo || ab > best) { best = ab; pick = (int)(q - lo); }  // R8: first wins
   }
   sp.tab[p] = (uint8_t)pick;
 }
 
+// Bucket starts L_j = floor(j*N/K)+1 for consecutive j without a division per step.
+struct PartIter {
+  int64_t L, rem, q, r, K;
+  __device__ PartIter(int64_t j, int64_t N, int64_t K_) : K(K_) {
+    q = N / K;
+    r = N - q * K;
+    const unsigned __int128 jn = (unsigned __int128)(uint64_t)j * (uint64_t)N;
+    const int64_t f = (int64_t)(jn / (uint64_t)K);
+    L = f + 1;
+    rem = (int64_t)(jn - (unsigned __int128)(uint64_t)f * (uint64_t)K);
+  }
+  __device__ void next() {  // j -> j+1
+    L += q;
+    rem += r;
+    if (rem >= K) {
+      rem -= K;
+      L += 1;
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ Batch bt) {
-  __shared__ uint8_t F[2][kChainThreads][kTableMaxBucket];
+  // F[c][ia][t]: thread t's map, entry ia (entry-major, so a warp touches 32
+  // consecutive bytes per entry instead of 32 bytes apart)
+  __shared__ uint8_t F[2][kTableMaxBucket][kChainThreads];
   __shared__ uint8_t dom[2][kChainThreads];
+  extern __shared__ uint4 s_tab4[];
+  pdl_wait();
+  pdl_trigger();
   const SeriesPlan& sp = plan_of(bt, blockIdx.x);
   const int tid = threadIdx.x;
   if (sp.branch == BR_ARANGE) {
@@ -113,17 +175,31 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
   const int64_t K = sp.n_out - 2, N = m - 2;
   const int T = K < kChainThreads ? (int)K : kChainThreads;
   const uint8_t* tab = sp.tab;
+  if (m <= bt.chain_smem) {  // stage the tables (16-byte aligned storage, padded to 16)
+    const int64_t nv = (m + 15) / 16;
+    const uint4* src = (const uint4*)sp.tab;
+    for (int64_t i = tid; i < nv; i += blockDim.x) s_tab4[i] = src[i];
+    __syncthreads();
+    tab = (const uint8_t*)s_tab4;
+  }
   int64_t j0 = 0, j1 = 0;
   if (tid < T) {
     j0 = muldiv(tid, K, T);
     j1 = muldiv(tid + 1, K, T);
     // Phase 1: compose this segment's steps for every possible entry offset.
-    const int d0 = j0 == 0 ? 1 : (int)(part_start(j0, N, K) - part_start(j0 - 1, N, K));
-    for (int ia = 0; ia < d0; ++ia) F[0][tid][ia] = (uint8_t)ia;
-    int64_t lprev = j0 == 0 ? 0 : part_start(j0 - 1, N, K);
+    PartIter it(j0 > 0 ? j0 - 1 : 0, N, K);  // start of bucket j0-1 (or of bucket 0)
+    int d0 = 1;
+    int64_t lprev = 0;
+    if (j0 > 0) {
+      lprev = it.L;
+      it.next();
+      d0 = (int)(it.L - lprev);
+    }
+    for (int ia = 0; ia < d0; ++ia) F[0][ia][tid] = (uint8_t)ia;
     for (int64_t j = j0; j < j1; ++j) {
-      for (int ia = 0; ia < d0; ++ia) F[0][tid][ia] = tab[lprev + F[0][tid][ia]];
-      lprev = part_start(j, N, K);
+      for (int ia = 0; ia < d0; ++ia) F[0][ia][tid] = tab[lprev + F[0][ia][tid]];
+      lprev = it.L;  // start of bucket j
+      it.next();
     }
     dom[0][tid] = (uint8_t)d0;
   }
@@ -134,27 +210,35 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
     if (tid < T) {
       if (tid >= d) {
         const int dd = dom[c][tid - d];
-        for (int ia = 0; ia < dd; ++ia) F[c ^ 1][tid][ia] = F[c][tid][F[c][tid - d][ia]];
+        for (int ia = 0; ia < dd; ++ia) F[c ^ 1][ia][tid] = F[c][F[c][ia][tid - d]][tid];
         dom[c ^ 1][tid] = (uint8_t)dd;
       } else {
         const int dd = dom[c][tid];
-        for (int ia = 0; ia < dd; ++ia) F[c ^ 1][tid][ia] = F[c][tid][ia];
+        for (int ia = 0; ia < dd; ++ia) F[c ^ 1][ia][tid] = F[c][ia][tid];
         dom[c ^ 1][tid] = (uint8_t)dd;
       }
     }
     c ^= 1;
   }
   __syncthreads();
-  // Phase 3: walk each segment from its resolved entry and write the picks.
+  // Phase 3: walk each segment from its resolved entry; first record the picked
+  // positions, then translate them to indices with independent loads.
   if (tid < T) {
-    int v = tid == 0 ? 0 : F[c][tid - 1][0];
-    int64_t lprev = j0 == 0 ? 0 : part_start(j0 - 1, N, K);
-    for (int64_t j = j0; j < j1; ++j) {
-      const int64_t lj = part_start(j, N, K);
-      v = tab[lprev + v];
-      sp.out[j + 1] = index_of(sp, lj + v);
-      lprev = lj;
+    int v = tid == 0 ? 0 : F[c][0][tid - 1];
+    PartIter it(j0 > 0 ? j0 - 1 : 0, N, K);
+    int64_t lprev = 0;
+    if (j0 > 0) {
+      lprev = it.L;
+      it.next();
     }
+    for (int64_t j = j0; j < j1; ++j) {
+      v = tab[lprev + v];
+      sp.out[j + 1] = it.L + v;  // position in bucket j
+      lprev = it.L;
+      it.next();
+    }
+    if (sp.sel)
+      for (int64_t j = j0; j < j1; ++j) sp.out[j + 1] = sp.sel[sp.out[j + 1]];
   }
   if (tid == 0) {
     sp.out[0] = index_of(sp, 0);
@@ -283,6 +367,8 @@ __global__ void __launch_bounds__(kGridThreads) k_lttb_grid(const __grid_constan
 
 // Sequential LTTB with one CTA per series (batched series with large buckets).
 __global__ void __launch_bounds__(kGridThreads) k_lttb_block(const __grid_constant__ Batch bt) {
+  pdl_wait();
+  pdl_trigger();
   const SeriesPlan& sp = plan_of(bt, blockIdx.x);
   if (sp.engine != EN_BLOCK) return;
   if (sp.branch != BR_LTTB_ALL && sp.branch != BR_MINMAX_LTTB) return;
@@ -337,15 +423,24 @@ int lttb_grid_blocks_per_sm() {
 
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st) {
   if (bt.total_slots <= 0) return cudaSuccess;
-  const int64_t grid = (bt.total_slots + 255) / 256;
-  k_tables<<<(unsigned)grid, 256, 0, st>>>(bt);
-  return cudaGetLastError();
+  const int64_t grid = (bt.total_slots + kTableThreads - 1) / kTableThreads;
+  return launch_pdl(k_tables, dim3((unsigned)grid), dim3(kTableThreads), 0, st, bt);
 }
 
-cudaError_t launch_chain(const Batch& bt, int n_blocks, cudaStream_t st) {
+cudaError_t launch_chain(const Batch& bt, int n_blocks, int64_t max_positions, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
-  k_chain<<<n_blocks, kChainThreads, 0, st>>>(bt);
-  return cudaGetLastError();
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmemMax);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
+  }
+  Batch b = bt;
+  b.chain_smem = max_positions <= kChainSmemMax ? ((max_positions + 15) & ~int64_t(15)) : 0;
+  return launch_pdl(k_chain, dim3(n_blocks), dim3(kChainThreads), (size_t)b.chain_smem, st, b);
 }
 
 cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_t st) {
@@ -365,8 +460,7 @@ cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st) {
 
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
-  k_lttb_block<<<n_blocks, kGridThreads, 0, st>>>(bt);
-  return cudaGetLastError();
+  return launch_pdl(k_lttb_block, dim3(n_blocks), dim3(kGridThreads), 0, st, bt);
 }
 
 }  // namespace mmlttb

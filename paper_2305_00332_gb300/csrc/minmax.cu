@@ -9,9 +9,9 @@
 //            a per-lane first-occurrence argmin/argmax, then reduces across the warp
 //            and writes one Record at slot (global bin + warp).  x is never streamed:
 //            bin bounds come from integer arithmetic (index bins) or from k_edges.
-//  k_merge   one CTA per series: combines the records of each bin (they sit in
-//            consecutive slots), drops empty bins, dedupes argmin == argmax and
-//            compacts [0, per-bin pairs..., n-1] with a block-wide scan.
+//  k_bins / k_binscan / k_place   compaction: combine each bin's records (they sit
+//            in consecutive slots), drop empty bins, dedupe argmin == argmax and place
+//            [0, per-bin pairs..., n-1] with a scan restarted at every series.
 #include "common.cuh"
 
 namespace mmlttb {
@@ -24,7 +24,7 @@ constexpr unsigned kFull = 0xffffffffu;
 #define MMLTTB_STREAM_UNROLL 4
 #endif
 #ifndef MMLTTB_STREAM_MIN_BLOCKS
-#define MMLTTB_STREAM_MIN_BLOCKS 1
+#define MMLTTB_STREAM_MIN_BLOCKS 4
 #endif
 constexpr int kUnroll = MMLTTB_STREAM_UNROLL;  // 16-byte vectors in flight per lane
 
@@ -64,12 +64,13 @@ __device__ __forceinline__ float fmax_nan(float a, float b) {
 __device__ __forceinline__ float proxy_of_hi(unsigned hi) { return __uint_as_float(hi); }
 
 // Bin bounds of series sp (R2 index bins; R3 x-width bins via the edge array).
+// Bins cover the points [p0, p0 + nb): the interior for MinMax, all points for M4.
 __device__ __forceinline__ int64_t bin_start(const Batch& bt, const SeriesPlan& sp, int64_t b) {
-  if (sp.binmode == MMLTTB_BINS_INDEX) return part_start(b, sp.n - 2, sp.B);
+  if (sp.binmode == MMLTTB_BINS_INDEX) return sp.p0 + muldiv(b, sp.nb, sp.B);
   return bt.edges[sp.edge_off + b];
 }
 __device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesPlan& sp, int64_t p) {
-  if (sp.binmode == MMLTTB_BINS_INDEX) return part_of(p, sp.n - 2, sp.B);
+  if (sp.binmode == MMLTTB_BINS_INDEX) return part_of(p - sp.p0 + 1, sp.nb, sp.B);
   return upper_index(bt.edges + sp.edge_off, (int)sp.B, p);
 }
 
@@ -205,13 +206,19 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane)
   return r;
 }
 
+// Smallest interior point q in [0, N] whose work unit floor(q*D/N) is >= t, for
+// 0 <= t <= D: ceil(t*N/D).
+__device__ __forceinline__ int64_t point_at_work(int64_t t, int64_t N, int64_t D) {
+  return muldiv_ceil(t, N, D);
+}
+
 // One warp over the interior points [p_lo, p_hi) of one series.
 __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t p_lo,
                                   int64_t p_hi, int64_t w, int lane) {
   int64_t b = bin_containing(bt, sp, p_lo);
   for (;;) {
     const int64_t sb = bin_start(bt, sp, b);
-    const int64_t sb1 = (b + 1 >= sp.B) ? sp.n - 1 : bin_start(bt, sp, b + 1);
+    const int64_t sb1 = (b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1);
     const int64_t lo = sb > p_lo ? sb : p_lo;
     const int64_t hi = sb1 < p_hi ? sb1 : p_hi;
     if (lo < hi) {
@@ -225,6 +232,8 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
 }
 
 __global__ void __launch_bounds__(kStreamThreads, MMLTTB_STREAM_MIN_BLOCKS) k_stream(const __grid_constant__ Batch bt) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
   if (w >= bt.n_warps) return;
@@ -236,16 +245,21 @@ __global__ void __launch_bounds__(kStreamThreads, MMLTTB_STREAM_MIN_BLOCKS) k_st
     const int64_t send = sp.pos_off + sp.npos;
     const int64_t seg_end = send < g_end ? send : g_end;
     if (seg_end > g) {
-      warp_series_range(bt, sp, 1 + (g - sp.pos_off), 1 + (seg_end - sp.pos_off), w, lane);
+      // binned points whose work unit lies in [g, seg_end): p0 + q, q in [q_lo, q_hi)
+      const int64_t q_lo = point_at_work(g - sp.pos_off, sp.nb, sp.npos);
+      const int64_t q_hi = point_at_work(seg_end - sp.pos_off, sp.nb, sp.npos);
+      if (q_hi > q_lo) warp_series_range(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
       g = seg_end;
     }
     ++s;
   }
 }
 
-// One warp per bin edge of every x-width series: S_b = first interior point with
-// x >= e_b, e_b = x_0 + floor(b (x_{n-1} - x_0) / B) (R3); S_0 = 1, S_B = n-1.
+// One warp per bin edge of every x-width series: S_b = first binned point with
+// x >= e_b, e_b = x_0 + floor(b (x_{n-1} - x_0) / B) (R3, R16); S_0 = p0, S_B = p0 + nb.
 __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= bt.total_edges) return;
@@ -253,16 +267,16 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
   const SeriesPlan& sp = plan_of(bt, s);
   const int64_t b = e - sp.edge_off;
   int64_t res;
-  if (sp.n < 3 || b == 0) {
-    res = 1;
+  if (sp.nb < 1 || b == 0) {
+    res = sp.p0;
   } else if (b >= sp.B) {
-    res = sp.n - 1;
+    res = sp.p0 + sp.nb;
   } else {
     const long long* x = (const long long*)sp.x;
     const long long x0 = __ldg(x), xl = __ldg(x + sp.n - 1);
     const long long D = xl - x0;
     const long long eb = x0 + (long long)muldiv(b, D, sp.B);
-    int64_t lo = 1, hi = sp.n - 1;  // answer in [lo, hi]
+    int64_t lo = sp.p0, hi = sp.p0 + sp.nb;  // answer in [lo, hi]
     while (hi - lo > 32) {
       const int64_t step = (hi - lo + 31) / 32;
       const int64_t q = lo + (int64_t)lane * step;
@@ -321,51 +335,177 @@ __device__ int block_excl_scan(int v, int* excl) {
   return total;
 }
 
-constexpr int kMergeThreads = 1024;
+// ---- compaction (A-2): three grid-wide kernels --------------------------------
+// Every series' bins are laid out from a CTA boundary (kBinsPerCta bins per CTA).
+//   k_bins     one thread per bin: combine the bin's records (consecutive slots)
+//              into (lower, higher) of argmin/argmax, -1 for an empty bin; each CTA
+//              writes how many indices its bins emit.
+//   k_binscan  one CTA: exclusive scan of the CTA totals, restarted at every
+//              series; the last CTA of a series fixes its count m and the first
+//              and last entries of its preselected list.
+//   k_place    one thread per bin: block scan + CTA offset place the bin's indices
+//              (and, before LTTB, their x and y as FP64) in the preselected list.
 
-__global__ void __launch_bounds__(kMergeThreads) k_merge(const __grid_constant__ Batch bt) {
-  const SeriesPlan& sp = plan_of(bt, blockIdx.x);
-  if (sp.branch != BR_MINMAX_LTTB && sp.branch != BR_PRESELECT) return;
+__device__ __forceinline__ int emit_count(int64_t lo, int64_t hi) {
+  return lo < 0 ? 0 : (lo == hi ? 1 : 2);
+}
+// M4 emits the sorted distinct {first, lo, hi, last} (first <= lo <= hi <= last).
+__device__ __forceinline__ int m4_count(int64_t first, int64_t lo, int64_t hi, int64_t last) {
+  return lo < 0 ? 0 : 1 + (lo != first) + (hi != lo) + (last != hi);
+}
+
+__global__ void __launch_bounds__(kBinsPerCta) k_bins(const __grid_constant__ Batch bt) {
+  __shared__ int s_series;
+  pdl_wait();
+  pdl_trigger();
+  const int64_t c = blockIdx.x;
+  if (threadIdx.x == 0) s_series = bt.cta_offs ? upper_index(bt.cta_offs, bt.n_series, c) : 0;
+  __syncthreads();
+  const SeriesPlan& sp = plan_of(bt, s_series);
+  const int64_t b = (c - sp.bincta_off) * kBinsPerCta + threadIdx.x;
+  int64_t lo = -1, hi = -1, first = -1, last = -1;
+  if (sp.nb > 0 && b < sp.B) {
+    const int64_t sb = bin_start(bt, sp, b);
+    const int64_t sb1 = (b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1);
+    if (sb < sb1) {
+      first = sb;
+      last = sb1 - 1;
+      const int64_t wf = warp_of(sp.pos_off + muldiv(sb - sp.p0, sp.npos, sp.nb), bt.total_pos, bt.n_warps);
+      const int64_t wl = warp_of(sp.pos_off + muldiv(sb1 - 1 - sp.p0, sp.npos, sp.nb), bt.total_pos, bt.n_warps);
+      const Record* rb = bt.rec + sp.bin_off + b;
+      Record r = rb[wf];
+      for (int64_t w = wf + 1; w <= wl; ++w) combine(r, rb[w]);
+      lo = r.imin < r.imax ? r.imin : r.imax;
+      hi = r.imin < r.imax ? r.imax : r.imin;
+    }
+  }
+  const int64_t slot = c * kBinsPerCta + threadIdx.x;
+  bt.binres[2 * slot] = lo;
+  bt.binres[2 * slot + 1] = hi;
+  int cnt = sp.branch == BR_M4 ? m4_count(first, lo, hi, last) : emit_count(lo, hi);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
+  __shared__ int s_warp[kBinsPerCta / 32];
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < kBinsPerCta / 32; ++w) t += s_warp[w];
+    bt.cta_sum[c] = t;
+    bt.cta_series[c] = s_series;
+  }
+}
+
+constexpr int kScanThreads = 1024;
+
+// Write the list head/tail of series s once its count m is known.
+__device__ void finish_series(const SeriesPlan& sp, int64_t emitted) {
   int64_t* P = sp.sel;
   const int64_t n = sp.n;
-  if (n <= 2) {  // no interior points: [0] or [0, 1]
-    if (threadIdx.x < n) P[threadIdx.x] = threadIdx.x;
-    if (threadIdx.x == 0) {
-      *sp.m_ptr = n;
-      if (sp.branch == BR_PRESELECT && sp.out_count) *sp.out_count = n;
+  int64_t m;
+  if (sp.branch == BR_M4) {  // M4 keeps no extra points
+    m = emitted;
+  } else if (n <= 2) {  // no interior points: [0] or [0, 1]
+    m = n;
+    for (int64_t i = 0; i < n; ++i) P[i] = i;
+  } else {
+    m = emitted + 2;
+    P[0] = 0;
+    P[m - 1] = n - 1;
+  }
+  if (sp.px && m > 0) {
+    sp.px[0] = x_of(sp, 0);
+    sp.py[0] = y_of(sp, 0);
+    sp.px[m - 1] = x_of(sp, n - 1);
+    sp.py[m - 1] = y_of(sp, n - 1);
+  }
+  *sp.m_ptr = m;
+  if ((sp.branch == BR_PRESELECT || sp.branch == BR_M4) && sp.out_count) *sp.out_count = m;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_binscan(const __grid_constant__ Batch bt) {
+  __shared__ int64_t s_inc[kScanThreads];
+  __shared__ int s_head[kScanThreads];
+  pdl_wait();
+  pdl_trigger();
+  const int tid = threadIdx.x;
+  const int64_t total = bt.total_bin_ctas;
+  int64_t carry = 0;  // running sum of the segment that continues into the next tile
+  for (int64_t tile = 0; tile < total; tile += kScanThreads) {
+    const int64_t c = tile + tid;
+    const bool valid = c < total;
+    const int s = valid ? bt.cta_series[c] : -1;
+    const int64_t v = valid ? bt.cta_sum[c] : 0;
+    const bool head = valid && (c == 0 || bt.cta_series[c - 1] != s);
+    s_inc[tid] = v;
+    s_head[tid] = head ? tid : -1;
+    __syncthreads();
+    // Hillis-Steele inclusive sum and max-scan of segment heads over the tile
+    for (int d = 1; d < kScanThreads; d <<= 1) {
+      const int64_t a = tid >= d ? s_inc[tid - d] : 0;
+      const int h = tid >= d ? s_head[tid - d] : -1;
+      __syncthreads();
+      s_inc[tid] += a;
+      if (h > s_head[tid]) s_head[tid] = h;
+      __syncthreads();
     }
+    const int start = s_head[tid];  // this element's segment start in the tile, or -1
+    int64_t excl = s_inc[tid] - v;
+    if (start >= 0) excl -= start > 0 ? s_inc[start - 1] : 0;
+    else excl += carry;
+    const int last = (int)((total - tile < kScanThreads ? total - tile : kScanThreads) - 1);
+    const int last_start = s_head[last];
+    const int64_t new_carry = last_start >= 0
+                                  ? s_inc[last] - (last_start > 0 ? s_inc[last_start - 1] : 0)
+                                  : carry + s_inc[last];
+    if (valid) {
+      bt.cta_off[c] = excl;
+      const bool tail = c + 1 == total || bt.cta_series[c + 1] != s;
+      if (tail) finish_series(plan_of(bt, s), excl + v);
+    }
+    __syncthreads();
+    carry = new_carry;
+  }
+}
+
+__global__ void __launch_bounds__(kBinsPerCta) k_place(const __grid_constant__ Batch bt) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t c = blockIdx.x;
+  const int s = bt.cta_series[c];
+  const SeriesPlan& sp = plan_of(bt, s);
+  const int64_t slot = c * kBinsPerCta + threadIdx.x;
+  const int64_t lo = bt.binres[2 * slot], hi = bt.binres[2 * slot + 1];
+  const bool m4 = sp.branch == BR_M4;
+  int64_t first = -1, last = -1;
+  if (m4 && lo >= 0) {
+    const int64_t b = (c - sp.bincta_off) * kBinsPerCta + threadIdx.x;
+    first = bin_start(bt, sp, b);
+    last = ((b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1)) - 1;
+  }
+  const int cnt = m4 ? m4_count(first, lo, hi, last) : emit_count(lo, hi);
+  int excl;
+  block_excl_scan<kBinsPerCta>(cnt, &excl);
+  if (cnt == 0 || (!m4 && sp.n <= 2)) return;
+  if (m4) {
+    int64_t o = bt.cta_off[c] + excl;
+    sp.sel[o++] = first;
+    if (lo != first) sp.sel[o++] = lo;
+    if (hi != lo) sp.sel[o++] = hi;
+    if (last != hi) sp.sel[o++] = last;
     return;
   }
-  int64_t base = 0;
-  for (int64_t tile = 0; tile < sp.B; tile += kMergeThreads) {
-    const int64_t b = tile + threadIdx.x;
-    int cnt = 0;
-    int64_t lo_i = 0, hi_i = 0;
-    if (b < sp.B) {
-      const int64_t sb = bin_start(bt, sp, b);
-      const int64_t sb1 = (b + 1 >= sp.B) ? n - 1 : bin_start(bt, sp, b + 1);
-      if (sb < sb1) {
-        const int64_t wf = warp_of(sp.pos_off + sb - 1, bt.total_pos, bt.n_warps);
-        const int64_t wl = warp_of(sp.pos_off + sb1 - 2, bt.total_pos, bt.n_warps);
-        const Record* rb = bt.rec + sp.bin_off + b;
-        Record r = rb[wf];
-        for (int64_t w = wf + 1; w <= wl; ++w) combine(r, rb[w]);
-        lo_i = r.imin < r.imax ? r.imin : r.imax;
-        hi_i = r.imin < r.imax ? r.imax : r.imin;
-        cnt = lo_i == hi_i ? 1 : 2;
-      }
+  const int64_t pos = 1 + bt.cta_off[c] + excl;
+  sp.sel[pos] = lo;
+  if (cnt == 2) sp.sel[pos + 1] = hi;
+  if (sp.px) {
+    sp.px[pos] = x_of(sp, lo);
+    sp.py[pos] = y_of(sp, lo);
+    if (cnt == 2) {
+      sp.px[pos + 1] = x_of(sp, hi);
+      sp.py[pos + 1] = y_of(sp, hi);
     }
-    int excl;
-    const int total = block_excl_scan<kMergeThreads>(cnt, &excl);
-    if (cnt > 0) P[1 + base + excl] = lo_i;
-    if (cnt > 1) P[2 + base + excl] = hi_i;
-    base += total;
-  }
-  if (threadIdx.x == 0) {
-    P[0] = 0;
-    P[1 + base] = n - 1;
-    *sp.m_ptr = base + 2;
-    if (sp.branch == BR_PRESELECT && sp.out_count) *sp.out_count = base + 2;
   }
 }
 
@@ -382,20 +522,22 @@ cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
   if (bt.total_edges <= 0) return cudaSuccess;
   const int64_t threads = bt.total_edges * 32;
   const int64_t grid = (threads + 255) / 256;
-  k_edges<<<(unsigned)grid, 256, 0, st>>>(bt);
-  return cudaGetLastError();
+  return launch_pdl(k_edges, dim3((unsigned)grid), dim3(256), 0, st, bt);
 }
 
 cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st) {
   if (bt.n_warps <= 0) return cudaSuccess;
-  k_stream<<<(unsigned)grid, kStreamThreads, 0, st>>>(bt);
-  return cudaGetLastError();
+  return launch_pdl(k_stream, dim3((unsigned)grid), dim3(kStreamThreads), 0, st, bt);
 }
 
-cudaError_t launch_merge(const Batch& bt, int n_blocks, cudaStream_t st) {
-  if (n_blocks <= 0) return cudaSuccess;
-  k_merge<<<n_blocks, kMergeThreads, 0, st>>>(bt);
-  return cudaGetLastError();
+cudaError_t launch_compact(const Batch& bt, cudaStream_t st) {
+  if (bt.total_bin_ctas <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)bt.total_bin_ctas);
+  cudaError_t e = launch_pdl(k_bins, grid, dim3(kBinsPerCta), 0, st, bt);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(k_binscan, dim3(1), dim3(kScanThreads), 0, st, bt);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_place, grid, dim3(kBinsPerCta), 0, st, bt);
 }
 
 }  // namespace mmlttb

@@ -323,6 +323,52 @@ def check_constant_series(o):
         assert list(pre) == expect
 
 
+def m4_members_index(n, B):
+    """Point p (0..n-1) lies in bin ceil((p+1)*B/n) - 1: the bins [floor(i n/B), floor((i+1) n/B))."""
+    bins = [[] for _ in range(B)]
+    for p in range(n):
+        bins[-(-(p + 1) * B // n) - 1].append(p)
+    return bins
+
+
+def m4_members_xwidth(x, B):
+    """Point p lies in the largest bin i with x0 + floor(i*D/B) <= x_p (all points)."""
+    x = [int(v) for v in x]
+    x0, D = x[0], x[-1] - x[0]
+    edges = [x0 + (i * D) // B for i in range(B)]
+    bins = [[] for _ in range(B)]
+    for p in range(len(x)):
+        bins[max(k for k in range(B) if edges[k] <= x[p])].append(p)
+    return bins
+
+
+def m4_reference(y, bins):
+    out = []
+    for members in bins:
+        if not members:
+            continue
+        a, b = members[0], members[-1] + 1
+        seg = np.asarray(y[a:b])
+        out.extend(sorted({a, a + int(np.argmin(seg)), a + int(np.argmax(seg)), b - 1}))
+    return out
+
+
+def check_m4(o):
+    """M4 against numpy argmin/argmax plus the bins' first and last members."""
+    for seed in range(5):
+        r = rng(800 + seed)
+        for n in (1, 2, 3, 7, 40, 333):
+            for y in _series_zoo(seed * 31 + n, n):
+                for n_out in (4, 5, 8, 12, 4 * n + 4, 101):
+                    B = n_out // 4
+                    assert list(o.m4(y, n_out)) == m4_reference(y, m4_members_index(n, B)), (n, n_out)
+                if n >= 2:
+                    x = _increasing_x(r, n, repeats=seed % 2 == 1)
+                    for n_out in (4, 12, 40):
+                        got = o.m4(y, n_out, x=x, binmode="xwidth")
+                        assert list(got) == m4_reference(y, m4_members_xwidth(x, n_out // 4)), (n, n_out)
+
+
 ALL_CHECKS = [
     check_worked_examples,
     check_minmax_index_bins,
@@ -333,4 +379,5 @@ ALL_CHECKS = [
     check_invariants,
     check_symmetries,
     check_constant_series,
+    check_m4,
 ]

@@ -20,6 +20,8 @@ def oracle_result(ref, s):
     op = s.get("op", "minmaxlttb")
     if op == "lttb":
         return ref.lttb(y, s["n_out"], x=x)
+    if op == "m4":
+        return ref.m4(y, s["n_out"], x=x, binmode=s.get("binmode", "index"))
     if op == "preselect":
         return ref.minmax_preselect(y, s["n_out"], s.get("r_ps", 4), x=x, binmode=s.get("binmode", "index"))
     return ref.minmaxlttb(y, s["n_out"], s.get("r_ps", 4), x=x, binmode=s.get("binmode", "index"))
@@ -35,7 +37,7 @@ def mixed_series(seed, count):
             r.integers(-3, 4, n).astype(dt)
         s = {"y_h": y, "n_out": int(r.choice([3, 4, 10, 57, 200, 1000, 4000])),
              "r_ps": int(r.choice([2, 3, 4, 8])),
-             "op": str(r.choice(["minmaxlttb", "minmaxlttb", "lttb", "preselect"]))}
+             "op": str(r.choice(["minmaxlttb", "minmaxlttb", "lttb", "preselect", "m4"]))}
         if s["op"] == "lttb" and n > s["n_out"] and (n - 2) // max(1, s["n_out"] - 2) > 2000:
             s["n_out"] = max(3, n // 1000)  # keep plain-LTTB buckets modest in a batch
         if n >= 3 and r.random() < 0.4:

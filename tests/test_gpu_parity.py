@@ -236,3 +236,40 @@ def test_single_series_1e9_xwidth(mm, ref):
     torch.cuda.empty_cache()
     eq(pre, ref.minmax_preselect(y, 4000, 4, x=x, binmode="xwidth"), "1e9 preselect")
     eq(got, ref.minmaxlttb(y, 4000, 4, x=x, binmode="xwidth"), "1e9 minmaxlttb")
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_point(mm, ref, pinned):
+    """mmlttb_minmaxlttb_host: pinned host inputs are read in place (zero-copy),
+    pageable ones are staged; both equal the device entry point and the oracle."""
+    n = 3_000_001
+    y = synth.random_walk(n, seed=21, dtype=np.float64)
+    x = synth.exp_gaps_x(n, seed=21, mean_gap=100.0, big_gaps=3, big_gap=10**8)
+    yh, xh = torch.from_numpy(y), torch.from_numpy(x)
+    if pinned:
+        yh, xh = yh.pin_memory(), xh.pin_memory()
+    for n_out, r_ps, bm, xx in ((2000, 4, "xwidth", xh), (700, 6, "index", None)):
+        got = mm.minmaxlttb_host(yh, n_out, r_ps, x=xx, binmode=bm).numpy()
+        exp = ref.minmaxlttb(y, n_out, r_ps, x=x if xx is not None else None, binmode=bm)
+        eq(got, exp, f"host entry pinned={pinned} {bm}")
+        dev_res = mm.minmaxlttb(dev(y), n_out, r_ps, x=dev(x) if xx is not None else None, binmode=bm)
+        eq(dev_res, exp, "device entry")
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 7, 100, 4097, 100_003])
+@pytest.mark.parametrize("kind", ["walk32", "walk64", "ties32", "zeros64", "const32"])
+def test_m4_index_bins(mm, ref, n, kind):
+    y = make(kind, n)
+    yd = dev(y)
+    for n_out in (4, 5, 8, 100, 4 * n + 4, 1001):
+        eq(mm.m4(yd, n_out), ref.m4(y, n_out), f"m4 n={n} {kind} n_out={n_out}")
+
+
+@pytest.mark.parametrize("n", [2, 9, 1000, 100_003])
+@pytest.mark.parametrize("repeats", [False, True])
+def test_m4_xwidth_bins(mm, ref, n, repeats):
+    y = make("walk64", n)
+    x = increasing_x(n, 7 * n, repeats=repeats)
+    for n_out in (4, 12, 400, 4000):
+        eq(mm.m4(dev(y), n_out, x=dev(x), binmode="xwidth"),
+           ref.m4(y, n_out, x=x, binmode="xwidth"), f"m4 xwidth n={n} n_out={n_out}")
