@@ -56,12 +56,19 @@ extern "C" {
 /* Kind of x. */
 #define MMLTTB_X_IMPLICIT 0 /* x = index; the x pointer is ignored (may be NULL) */
 #define MMLTTB_X_I64 1      /* int64, non-decreasing */
-#define MMLTTB_X_F64 2      /* float64, non-decreasing (index bins only) */
+#define MMLTTB_X_F64 2      /* float64, non-decreasing, finite */
 
 /* How MinMax bins partition the interior points 1..n_in-2. */
 #define MMLTTB_BINS_INDEX 0  /* equal count: bin i = [floor(i(n-2)/B)+1, floor((i+1)(n-2)/B)+1) */
-#define MMLTTB_BINS_XWIDTH 1 /* equal x width (int64 x only): edges e_i = x0 + floor(i(x_{n-1}-x0)/B);
-                                point p is in the largest bin i with e_i <= x_p; empty bins emit nothing */
+#define MMLTTB_BINS_XWIDTH 1 /* equal x width: edges e_i = x0 + floor(i(x_{n-1}-x0)/B) for int64 x,
+                                e_i = x0 + (i*(x_{n-1}-x0))/B in FP64 (each operation rounded) for
+                                float64 x; point p is in the largest bin i with e_i <= x_p;
+                                empty bins emit nothing */
+
+/* Flag OR-ed into binmode of mmlttb_minmax_preselect and mmlttb_m4 (only): NaN-aware
+   bins.  A bin holding a NaN reports its first NaN as both argmin and argmax (the
+   convention of numpy's argmin/argmax), so a plot of the selection shows the gap. */
+#define MMLTTB_NAN_AWARE 0x10
 
 /* Operation selector for mmlttb_workspace_bytes. */
 #define MMLTTB_OP_PRESELECT 0
@@ -320,6 +327,25 @@ int mmlttb_set_timing_events(void *start_event, void *stop_event);
  * compaction, LTTB tables, LTTB chain.
  */
 int mmlttb_set_stage_events(void *const *events, int count);
+
+/*
+ * Autotuning of the streaming MinMax kernel (the HBM-bound step).  The library
+ * carries several compiled variants of it, differing in 16-byte loads in flight
+ * per lane and in resident CTAs per SM (see mmlttb_stream_variant_info); the
+ * number of lanes that share a bin is chosen per series from its mean bin size.
+ * mmlttb_autotune times every variant on MinMax preselection of the caller's y
+ * (device, n_in values; index bins, n_out and r_ps as given; out_idx and the
+ * workspace as for mmlttb_minmax_preselect), blocking, and makes the fastest one
+ * the variant for that y type on the current device (*best_variant, *best_ms =
+ * its median kernel time).  The choice lasts for the process; get/set let a
+ * caller persist and restore it.
+ */
+int mmlttb_stream_variant_info(int variant, int *unroll, int *min_blocks);
+int mmlttb_autotune(int ydtype, const void *y, int64_t n_in, int64_t n_out, int32_t r_ps,
+                    int64_t *out_idx, int64_t out_cap, void *workspace, size_t workspace_bytes,
+                    mmlttb_stream stream, int *best_variant, float *best_ms);
+int mmlttb_get_stream_variant(int ydtype, int *variant);
+int mmlttb_set_stream_variant(int ydtype, int variant);
 
 /* Number of kernels this library has launched from the calling thread so far. */
 unsigned long long mmlttb_launch_count(void);

@@ -23,6 +23,7 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "
 F32, F64 = 0, 1
 X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1
+NAN_AWARE = 0x10
 
 
 def compile_oracle(src=SRC, out=LIB, extra=()):
@@ -88,9 +89,10 @@ class Oracle:
         raise TypeError(f"x dtype {x.dtype}")
 
     @staticmethod
-    def _bm(binmode):
-        return {"index": BINS_INDEX, "xwidth": BINS_XWIDTH, BINS_INDEX: BINS_INDEX,
-                BINS_XWIDTH: BINS_XWIDTH}[binmode]
+    def _bm(binmode, nan_aware=False):
+        bm = {"index": BINS_INDEX, "xwidth": BINS_XWIDTH, BINS_INDEX: BINS_INDEX,
+              BINS_XWIDTH: BINS_XWIDTH}[binmode]
+        return bm | (NAN_AWARE if nan_aware else 0)
 
     @staticmethod
     def _rc(r, what):
@@ -98,22 +100,22 @@ class Oracle:
             raise ValueError(f"oracle {what} returned {r}")
         return r
 
-    def minmax_bins(self, y, B, x=None, binmode="index"):
+    def minmax_bins(self, y, B, x=None, binmode="index", nan_aware=False):
         y, yd = self._y(y)
         x, xk, xp = self._x(x, len(y))
         imin = np.empty(B, np.int64)
         imax = np.empty(B, np.int64)
-        self._rc(self.lib.mmo_minmax_bins(y.ctypes.data, yd, xp, xk, len(y), B, self._bm(binmode),
+        self._rc(self.lib.mmo_minmax_bins(y.ctypes.data, yd, xp, xk, len(y), B, self._bm(binmode, nan_aware),
                                           imin.ctypes.data, imax.ctypes.data), "minmax_bins")
         return imin, imax
 
-    def minmax_preselect(self, y, n_out, r_ps, x=None, binmode="index"):
+    def minmax_preselect(self, y, n_out, r_ps, x=None, binmode="index", nan_aware=False):
         y, yd = self._y(y)
         x, xk, xp = self._x(x, len(y))
         B = max(n_out * r_ps // 2, 1)
         out = np.empty(2 * B + 2, np.int64)
         m = self._rc(self.lib.mmo_minmax_preselect(y.ctypes.data, yd, xp, xk, len(y), n_out, r_ps,
-                                                   self._bm(binmode), out.ctypes.data), "preselect")
+                                                   self._bm(binmode, nan_aware), out.ctypes.data), "preselect")
         return out[:m].copy()
 
     def lttb(self, y, n_out, x=None):
@@ -133,11 +135,11 @@ class Oracle:
                                                  n_out, out.ctypes.data), "lttb_positions")
         return out[:m].copy()
 
-    def m4(self, y, n_out, x=None, binmode="index"):
+    def m4(self, y, n_out, x=None, binmode="index", nan_aware=False):
         y, yd = self._y(y)
         x, xk, xp = self._x(x, len(y))
         out = np.empty(max(4 * (n_out // 4), 1), np.int64)
-        m = self._rc(self.lib.mmo_m4(y.ctypes.data, yd, xp, xk, len(y), n_out, self._bm(binmode),
+        m = self._rc(self.lib.mmo_m4(y.ctypes.data, yd, xp, xk, len(y), n_out, self._bm(binmode, nan_aware),
                                      out.ctypes.data), "m4")
         return out[:m].copy()
 

@@ -20,7 +20,7 @@
  *   - LTTB: per bucket B_i, the point forming the largest triangle with the
  *     point selected in B_{i-1} and the average (mean x, mean y) of B_{i+1}.
  *
- * Readings where the paper is silent (numbered R1..R15 wherever they are cited):
+ * Readings where the paper is silent (numbered R1..R18 wherever they are cited):
  *   R1  LTTB buckets: first and last point fixed, K = n_out-2 buckets over the
  *       interior positions 1..m-2, bucket j = [floor(j(m-2)/K)+1, floor((j+1)(m-2)/K)+1)
  *       in exact integer arithmetic.
@@ -51,6 +51,12 @@
  *       of each bin): B = floor(n_out/4) bins over ALL points 0..n-1, index bins
  *       [floor(i n/B), floor((i+1) n/B)), x-width bins as R3 but over all points;
  *       per non-empty bin the sorted distinct {first, argmin, argmax, last}.
+ *   R17 x-width bins on float64 x: D = x_{n-1} - x_0 and e_i = x_0 + (i*D)/B in FP64,
+ *       each operation rounded on its own; point p is in the largest bin i with
+ *       e_i <= x_p (FP64 comparison), as R3 otherwise.
+ *   R18 NaN-aware MinMax / M4 (binmode | NAN_AWARE): a bin that holds a NaN reports
+ *       its first NaN as both argmin and argmax (the convention of numpy's argmin and
+ *       argmax); other bins as R8.  Plain MinMax/LTTB keep R11.
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,6 +69,7 @@
 enum { Y_F32 = 0, Y_F64 = 1 };
 enum { X_IMPLICIT = 0, X_I64 = 1, X_F64 = 2 };
 enum { BINS_INDEX = 0, BINS_XWIDTH = 1 };
+#define NAN_AWARE 0x10 /* flag OR-ed into binmode (R18) */
 
 /* The y value of point i as a double (a float converts exactly). */
 static double y_at(const void *y, int ydt, int64_t i)
@@ -108,19 +115,22 @@ int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n
 {
     int rc = check_common(y, ydt, x, xk, n);
     if (rc) return rc;
+    const int nan_aware = (binmode & NAN_AWARE) != 0;
+    binmode &= ~NAN_AWARE;
     if (B < 1) return MMO_EINVAL;
     if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
-    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk == X_IMPLICIT) return MMO_EINVAL;
 
     double *vmin = (double *)malloc(sizeof(double) * (size_t)B);
     double *vmax = (double *)malloc(sizeof(double) * (size_t)B);
-    if (!vmin || !vmax) { free(vmin); free(vmax); return MMO_ENOMEM; }
+    char *hasnan = (char *)calloc((size_t)B, 1);
+    if (!vmin || !vmax || !hasnan) { free(vmin); free(vmax); free(hasnan); return MMO_ENOMEM; }
     for (int64_t b = 0; b < B; b++) { imin[b] = -1; imax[b] = -1; }
 
     const int64_t N = n - 2; /* interior points 1..n-2 */
     const int64_t *xi = (const int64_t *)x;
     int64_t x0 = 0, D = 0;
-    if (binmode == BINS_XWIDTH && n >= 2) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
+    if (binmode == BINS_XWIDTH && xk == X_I64 && n >= 2) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
 
     /* start (index mode) or left edge (x mode) of bin b+1; past the last bin, a bound
        above every int64 */
@@ -128,19 +138,37 @@ int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n
     ((bb) + 1 >= B ? (__int128)INT64_MAX + 1                                            \
      : binmode == BINS_INDEX ? (__int128)part_start((bb) + 1, N, B)                     \
      : (__int128)x0 + ((__int128)((bb) + 1) * (__int128)D) / (__int128)B)
+    /* float64 x (R17): left edge of bin b+1 in FP64, +inf past the last bin */
+    const double *xf = (const double *)x;
+    const double xf0 = (binmode == BINS_XWIDTH && xk == X_F64 && n >= 2) ? xf[0] : 0.0;
+    const double Df = (binmode == BINS_XWIDTH && xk == X_F64 && n >= 2) ? xf[n - 1] - xf[0] : 0.0;
+#define NEXT_EDGE_F(bb) ((bb) + 1 >= B ? INFINITY : xf0 + ((double)((bb) + 1) * Df) / (double)B)
+    const int fx = binmode == BINS_XWIDTH && xk == X_F64;
     int64_t b = 0;
-    __int128 next = NEXT_BOUND(b);
+    __int128 next = fx ? 0 : NEXT_BOUND(b);
+    double nextf = fx ? NEXT_EDGE_F(b) : 0.0;
     for (int64_t p = 1; p <= n - 2; p++) {
+        if (fx) {
+            while (nextf <= xf[p]) {
+                b++;
+                nextf = NEXT_EDGE_F(b);
+            }
+        }
         /* Move to the last bin whose start is at or before p:
            index mode: start(b+1) <= p;  x mode: e_{b+1} = x_0 + floor((b+1) D / B) <= x_p (R3) */
-        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
-        while (next <= here) {
+        __int128 here = fx ? 0 : binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
+        while (!fx && next <= here) {
             b++;
             next = NEXT_BOUND(b);
         }
         double v = y_at(y, ydt, p);
         if (imin[b] < 0) {
             imin[b] = p; imax[b] = p; vmin[b] = v; vmax[b] = v;
+            if (nan_aware && isnan(v)) hasnan[b] = 1;
+        } else if (nan_aware && hasnan[b]) {
+            /* the bin's first NaN decides both extremes (R18) */
+        } else if (nan_aware && isnan(v)) {
+            hasnan[b] = 1; imin[b] = p; imax[b] = p;
         } else {
             /* strict comparisons keep the first occurrence (R8, R10) */
             if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }
@@ -148,8 +176,10 @@ int64_t mmo_minmax_bins(const void *y, int ydt, const void *x, int xk, int64_t n
         }
     }
 #undef NEXT_BOUND
+#undef NEXT_EDGE_F
     free(vmin);
     free(vmax);
+    free(hasnan);
     return B;
 }
 
@@ -168,8 +198,9 @@ int64_t mmo_minmax_preselect(const void *y, int ydt, const void *x, int xk, int6
     if (n_out > INT64_MAX / r_ps) return MMO_EINVAL;
     int64_t B = n_out * (int64_t)r_ps / 2;
     if (B < 1) return MMO_EINVAL;
-    if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
-    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    const int bm = binmode & ~NAN_AWARE;
+    if (bm != BINS_INDEX && bm != BINS_XWIDTH) return MMO_EINVAL;
+    if (bm == BINS_XWIDTH && xk == X_IMPLICIT) return MMO_EINVAL;
     if (n == 0) return 0;
     if (n == 1) { out[0] = 0; return 1; }
 
@@ -268,7 +299,7 @@ int64_t mmo_minmaxlttb(const void *y, int ydt, const void *x, int xk, int64_t n,
     if (rc) return rc;
     if (n_out < 0) return MMO_EINVAL;
     if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
-    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk == X_IMPLICIT) return MMO_EINVAL;
     if (n_out >= n) {
         for (int64_t p = 0; p < n; p++) out[p] = p;
         return n;
@@ -297,9 +328,11 @@ int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t
 {
     int rc = check_common(y, ydt, x, xk, n);
     if (rc) return rc;
+    const int nan_aware = (binmode & NAN_AWARE) != 0;
+    binmode &= ~NAN_AWARE;
     if (n_out < 4) return MMO_EINVAL;
     if (binmode != BINS_INDEX && binmode != BINS_XWIDTH) return MMO_EINVAL;
-    if (binmode == BINS_XWIDTH && xk != X_I64) return MMO_EINVAL;
+    if (binmode == BINS_XWIDTH && xk == X_IMPLICIT) return MMO_EINVAL;
     const int64_t B = n_out / 4;
     if (n == 0) return 0;
 
@@ -309,14 +342,19 @@ int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t
     int64_t *imax = (int64_t *)malloc(sizeof(int64_t) * (size_t)B);
     double *vmin = (double *)malloc(sizeof(double) * (size_t)B);
     double *vmax = (double *)malloc(sizeof(double) * (size_t)B);
-    if (!first || !last || !imin || !imax || !vmin || !vmax) {
-        free(first); free(last); free(imin); free(imax); free(vmin); free(vmax);
+    char *hasnan = (char *)calloc((size_t)B, 1);
+    if (!first || !last || !imin || !imax || !vmin || !vmax || !hasnan) {
+        free(first); free(last); free(imin); free(imax); free(vmin); free(vmax); free(hasnan);
         return MMO_ENOMEM;
     }
     for (int64_t b = 0; b < B; b++) first[b] = -1;
     const int64_t *xi = (const int64_t *)x;
     int64_t x0 = 0, D = 0;
-    if (binmode == BINS_XWIDTH) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
+    if (binmode == BINS_XWIDTH && xk == X_I64) { x0 = xi[0]; D = xi[n - 1] - xi[0]; }
+    const double *xf = (const double *)x;
+    const int fx = binmode == BINS_XWIDTH && xk == X_F64;
+    const double xf0 = fx ? xf[0] : 0.0, Df = fx ? xf[n - 1] - xf[0] : 0.0;
+#define NEXT_EDGE_F4(bb) ((bb) + 1 >= B ? INFINITY : xf0 + ((double)((bb) + 1) * Df) / (double)B)
     /* start (index mode) or left edge (x mode) of bin b+1; past the last bin, a bound
        above every int64 */
 #define NEXT_BOUND4(bb)                                                                 \
@@ -324,23 +362,38 @@ int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t
      : binmode == BINS_INDEX ? (__int128)(((unsigned __int128)((bb) + 1) * (uint64_t)n) / (uint64_t)B) \
      : (__int128)x0 + ((__int128)((bb) + 1) * (__int128)D) / (__int128)B)
     int64_t b = 0;
-    __int128 next = NEXT_BOUND4(b);
+    __int128 next = fx ? 0 : NEXT_BOUND4(b);
+    double nextf = fx ? NEXT_EDGE_F4(b) : 0.0;
     for (int64_t p = 0; p < n; p++) {
-        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
-        while (next <= here) {
+        if (fx) {
+            while (nextf <= xf[p]) {
+                b++;
+                nextf = NEXT_EDGE_F4(b);
+            }
+        }
+        __int128 here = fx ? 0 : binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];
+        while (!fx && next <= here) {
             b++;
             next = NEXT_BOUND4(b);
         }
         double v = y_at(y, ydt, p);
         if (first[b] < 0) {
             first[b] = p; last[b] = p; imin[b] = p; imax[b] = p; vmin[b] = v; vmax[b] = v;
+            if (nan_aware && isnan(v)) hasnan[b] = 1;
         } else {
             last[b] = p;
-            if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }
-            if (v > vmax[b]) { vmax[b] = v; imax[b] = p; }
+            if (nan_aware && hasnan[b]) {
+                /* the bin's first NaN decides both extremes (R18) */
+            } else if (nan_aware && isnan(v)) {
+                hasnan[b] = 1; imin[b] = p; imax[b] = p;
+            } else {
+                if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }
+                if (v > vmax[b]) { vmax[b] = v; imax[b] = p; }
+            }
         }
     }
 #undef NEXT_BOUND4
+#undef NEXT_EDGE_F4
     int64_t m = 0;
     for (b = 0; b < B; b++) {
         if (first[b] < 0) continue;
@@ -349,6 +402,6 @@ int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t
         for (int k = 0; k < 4; k++)
             if (k == 0 || c[k] != c[k - 1]) out[m++] = c[k];
     }
-    free(first); free(last); free(imin); free(imax); free(vmin); free(vmax);
+    free(first); free(last); free(imin); free(imax); free(vmin); free(vmax); free(hasnan);
     return m;
 }

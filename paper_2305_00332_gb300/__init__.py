@@ -19,6 +19,7 @@ OK, EINVAL, ENOSPC, ECUDA, ETIMEOUT, ERANGE, EDEVICE, ENOMEM, ESCRATCH = 0, -1, 
 F32, F64 = 0, 1
 X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1
+NAN_AWARE = 0x10
 OP_PRESELECT, OP_LTTB, OP_MINMAXLTTB, OP_M4 = 0, 1, 2, 3
 
 if not os.path.exists(LIB_PATH):
@@ -57,6 +58,15 @@ lib.mmlttb_minmaxlttb_host.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _i32, _
 lib.mmlttb_set_timing_events.restype = _int
 lib.mmlttb_set_timing_events.argtypes = [_vp, _vp]
 lib.mmlttb_launch_count.restype = ctypes.c_ulonglong
+lib.mmlttb_stream_variant_info.restype = _int
+lib.mmlttb_stream_variant_info.argtypes = [_int, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+lib.mmlttb_autotune.restype = _int
+lib.mmlttb_autotune.argtypes = [_int, _vp, _i64, _i64, _i32, _vp, _i64, _vp, _sz, _vp, ctypes.POINTER(_int),
+                                ctypes.POINTER(ctypes.c_float)]
+lib.mmlttb_get_stream_variant.restype = _int
+lib.mmlttb_get_stream_variant.argtypes = [_int, ctypes.POINTER(_int)]
+lib.mmlttb_set_stream_variant.restype = _int
+lib.mmlttb_set_stream_variant.argtypes = [_int, _int]
 lib.mmlttb_set_stage_events.restype = _int
 lib.mmlttb_set_stage_events.argtypes = [ctypes.POINTER(_vp), _int]
 
@@ -97,11 +107,14 @@ def _xkind(x):
     raise TypeError(f"x must be int64 or float64, got {x.dtype}")
 
 
-def _binmode(binmode):
+def _binmode(binmode, nan_aware=False):
+    flag = NAN_AWARE if nan_aware else 0
+    if isinstance(binmode, int) and binmode & NAN_AWARE:
+        flag, binmode = NAN_AWARE, binmode & ~NAN_AWARE
     if binmode in (BINS_INDEX, "index"):
-        return BINS_INDEX
+        return BINS_INDEX | flag
     if binmode in (BINS_XWIDTH, "xwidth", "x"):
-        return BINS_XWIDTH
+        return BINS_XWIDTH | flag
     raise ValueError(f"unknown bin mode {binmode!r}")
 
 
@@ -139,12 +152,13 @@ def _finish(out, count, sync):
     return out[: int(count.item())]
 
 
-def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True):
+def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True,
+                     nan_aware=False):
     """MinMax preselection (mmlttb_minmax_preselect): int64 indices of point 0, the
     per-bin argmin/argmax of floor(n_out*r_ps/2) bins, and point n-1."""
     _check_inputs(y, x)
     n = y.numel()
-    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode)
+    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode, nan_aware)
     cap = min(n, (n_out * r_ps // 2) * 2 + 2)
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
@@ -157,12 +171,12 @@ def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, works
     return _finish(out, count, sync)
 
 
-def m4(y, n_out, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True):
+def m4(y, n_out, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True, nan_aware=False):
     """M4 (mmlttb_m4): per bin of floor(n_out/4) bins over all points, the first,
     argmin, argmax and last index, sorted and without repeats."""
     _check_inputs(y, x)
     n = y.numel()
-    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode)
+    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode, nan_aware)
     cap = min(n, 4 * (n_out // 4))
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
@@ -257,6 +271,72 @@ def set_timing_events(start, stop):
     _check(lib.mmlttb_set_timing_events(ctypes.c_void_p(start.cuda_event) if start is not None else None,
                                         ctypes.c_void_p(stop.cuda_event) if stop is not None else None),
            "mmlttb_set_timing_events")
+
+
+def stream_variants():
+    """[(unroll, min_blocks)] of the compiled stream-kernel variants."""
+    out = []
+    v = 0
+    while True:
+        u, b = _int(0), _int(0)
+        if lib.mmlttb_stream_variant_info(v, ctypes.byref(u), ctypes.byref(b)) != OK:
+            return out
+        out.append((u.value, b.value))
+        v += 1
+
+
+def _tune_cache_path():
+    return os.environ.get("MMLTTB_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "mmlttb_tuning.json"))
+
+
+def autotune(y, n_out=4000, r_ps=4, save=True):
+    """Time every stream-kernel variant on MinMax preselection of y (a CUDA tensor),
+    select the fastest for y's type on y's device, and record it in the tuning cache
+    (JSON keyed by device name and y type).  Returns (variant, median ms)."""
+    import json
+    _check_inputs(y, None)
+    yd = _ydt(y)
+    n = y.numel()
+    cap = min(n, (n_out * r_ps // 2) * 2 + 2)
+    out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    ws = torch.empty(workspace_bytes(OP_PRESELECT, yd, X_IMPLICIT, n, n_out, r_ps), dtype=torch.uint8,
+                     device=y.device)
+    v, ms = _int(0), ctypes.c_float(0.0)
+    with torch.cuda.device(y.device):
+        _check(lib.mmlttb_autotune(yd, y.data_ptr(), n, n_out, r_ps, out.data_ptr(), out.numel(),
+                                   ws.data_ptr(), ws.numel(), _stream(y.device), ctypes.byref(v),
+                                   ctypes.byref(ms)), "mmlttb_autotune")
+    if save:
+        path = _tune_cache_path()
+        try:
+            cache = json.load(open(path)) if os.path.exists(path) else {}
+        except (OSError, ValueError):
+            cache = {}
+        cache[f"{torch.cuda.get_device_name(y.device)}/{'f32' if yd == F32 else 'f64'}"] = v.value
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return v.value, ms.value
+
+
+def load_tuning(device=None):
+    """Apply the cached stream-kernel choices for `device` (if any were saved)."""
+    import json
+    path = _tune_cache_path()
+    if not os.path.exists(path):
+        return {}
+    cache = json.load(open(path))
+    device = torch.device(device if device is not None else "cuda")
+    name = torch.cuda.get_device_name(device)
+    applied = {}
+    with torch.cuda.device(device):
+        for yd, key in ((F32, "f32"), (F64, "f64")):
+            v = cache.get(f"{name}/{key}")
+            if v is not None:
+                _check(lib.mmlttb_set_stream_variant(yd, int(v)), "mmlttb_set_stream_variant")
+                applied[key] = v
+    return applied
 
 
 def set_stage_events(events):

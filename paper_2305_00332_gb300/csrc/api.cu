@@ -8,6 +8,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -47,9 +49,10 @@ int get_dev_info(DevInfo* out) {
     return MMLTTB_OK;
   }
   DevInfo d;
+  d.device = dev;
   e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(e);
-  d.stream_bps = stream_blocks_per_sm();
+  for (int v = 0; v < kStreamVariants; ++v) d.stream_bps[v] = stream_blocks_per_sm(v);
   d.grid_bps = lttb_grid_blocks_per_sm();
   d.ok = true;
   if (dev >= 0 && dev < 64) g_dev[dev] = d;
@@ -57,6 +60,32 @@ int get_dev_info(DevInfo* out) {
   return MMLTTB_OK;
 }
 
+// Tuned stream variant per device and y type; a per-thread override while tuning.
+std::atomic<int> g_variant[64][2];
+thread_local int g_variant_override = -1;
+
+int stream_variant(const DevInfo& d, int ydt) {
+  if (g_variant_override >= 0) return g_variant_override;
+  if (d.device < 0 || d.device >= 64 || ydt < 0 || ydt > 1) return 0;
+  return g_variant[d.device][ydt].load();
+}
+
+int64_t stream_warp_cap(const DevInfo& d) {
+  int64_t c = 0;
+  for (int v = 0; v < kStreamVariants; ++v) {
+    const int64_t w = (int64_t)d.sms * d.stream_bps[v] * kStreamWarps;
+    if (w > c) c = w;
+  }
+  return c;
+}
+
+int64_t stream_warps(const DevInfo& d, int variant, int64_t work) {
+  int64_t W = work / (kBinCostMax + 1);
+  const int64_t cap = (int64_t)d.sms * d.stream_bps[variant] * kStreamWarps;
+  if (W > cap) W = cap;
+  if (W < 1 && work > 0) W = 1;
+  return W;
+}
 
 struct SinglePlan {
   int32_t branch = BR_ARANGE, engine = EN_NONE;
@@ -66,9 +95,10 @@ struct SinglePlan {
   size_t off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, off_px = 0, off_py = 0;
   int64_t nct = 0;  // compaction CTAs
   int64_t nb = 0;   // binned points
+  int group = 32;   // lanes per bin in the stream
+  int variant = 0;  // stream-kernel variant
   size_t total = kHeader;
 };
-
 
 int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
              int32_t* branch, int64_t* bins) {
@@ -76,9 +106,13 @@ int classify(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, in
   if (xk != MMLTTB_X_IMPLICIT && xk != MMLTTB_X_I64 && xk != MMLTTB_X_F64) return MMLTTB_EINVAL;
   if (n < 0 || n_out < 0) return MMLTTB_EINVAL;
   const bool uses_bins = op == MMLTTB_OP_PRESELECT || op == MMLTTB_OP_MINMAXLTTB || op == MMLTTB_OP_M4;
+  if (binmode & MMLTTB_NAN_AWARE) {  // NaN-aware aggregation: MinMax preselection and M4 only
+    if (op != MMLTTB_OP_PRESELECT && op != MMLTTB_OP_M4) return MMLTTB_EINVAL;
+    binmode &= ~MMLTTB_NAN_AWARE;
+  }
   if (uses_bins) {
     if (binmode != MMLTTB_BINS_INDEX && binmode != MMLTTB_BINS_XWIDTH) return MMLTTB_EINVAL;
-    if (binmode == MMLTTB_BINS_XWIDTH && xk != MMLTTB_X_I64) return MMLTTB_EINVAL;
+    if (binmode == MMLTTB_BINS_XWIDTH && xk == MMLTTB_X_IMPLICIT) return MMLTTB_EINVAL;
   }
   int64_t B = 0;
   int32_t br;
@@ -122,15 +156,17 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
   SinglePlan p;
   int rc = classify(op, ydt, xk, n, n_out, r_ps, binmode, &p.branch, &p.B);
   if (rc) return rc;
+  binmode &= ~MMLTTB_NAN_AWARE;
   size_t off = kHeader;
   if (binned(p.branch)) {
     const int64_t N = p.branch == BR_M4 ? n : (n > 2 ? n - 2 : 0);
     p.nb = N;
-    p.npos = series_work(N, p.B);
-    p.Wcap = (int64_t)d.sms * d.stream_bps * kStreamWarps;
-    p.W = p.npos / (kBinCost + 1);  // every warp gets at least one point
-    if (p.W > p.Wcap) p.W = p.Wcap;
-    if (p.W < 1 && p.npos > 0) p.W = 1;
+    // x-width bins can be very uneven: keep whole warps per bin there
+    p.group = binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(N, p.B, ydt == MMLTTB_F32 ? 4 : 8);
+    p.npos = series_work(N, p.B, p.group);
+    p.Wcap = stream_warp_cap(d);
+    p.variant = stream_variant(d, ydt);
+    p.W = stream_warps(d, p.variant, p.npos);
     if (p.W > 0 && N / p.W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // per-warp span
     if (binmode == MMLTTB_BINS_XWIDTH) {
       p.off_edges = off;
@@ -211,6 +247,8 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.x = xk == MMLTTB_X_IMPLICIT ? nullptr : x;
   sp.ydt = ydt;
   sp.xk = xk;
+  sp.nan_aware = (binmode & MMLTTB_NAN_AWARE) ? 1 : 0;
+  binmode &= ~MMLTTB_NAN_AWARE;
   sp.binmode = binmode;
   sp.branch = p.branch;
   sp.engine = p.engine;
@@ -227,6 +265,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.m_ptr = (int64_t*)(w + 8);
   sp.p0 = p.branch == BR_M4 ? 0 : 1;
   sp.nb = p.nb;
+  sp.group = p.group;
   sp.sel = (p.branch == BR_PRESELECT || p.branch == BR_M4) ? out
            : (p.branch == BR_MINMAX_LTTB ? (int64_t*)(w + p.off_sel) : nullptr);
   sp.px = p.branch == BR_MINMAX_LTTB ? (double*)(w + p.off_px) : nullptr;
@@ -238,7 +277,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.out_count = out_count;
   bt.total_pos = p.npos;
   bt.n_warps = p.W;
-  bt.total_edges = (p.B > 0 && binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
+  bt.total_edges = (p.B > 0 && sp.binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
   bt.total_slots = p.tab_cap;
   bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
   bt.edges = p.off_edges ? (int64_t*)(w + p.off_edges) : nullptr;
@@ -270,7 +309,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
-      if ((e = launch_stream(bt, grid, st)) != cudaSuccess) return cuda_fail(e);
+      if ((e = launch_stream(bt, grid, p.variant, st)) != cudaSuccess) return cuda_fail(e);
       stage_mark(st);
       ++g_launches;
     }
@@ -477,6 +516,80 @@ int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, i
 }
 
 
+
+int mmlttb_stream_variant_info(int variant, int* unroll, int* min_blocks) {
+  if (!unroll || !min_blocks) return MMLTTB_EINVAL;
+  return stream_variant_info(variant, unroll, min_blocks) == 0 ? MMLTTB_OK : MMLTTB_EINVAL;
+}
+
+int mmlttb_get_stream_variant(int ydtype, int* variant) {
+  if (!variant || (ydtype != MMLTTB_F32 && ydtype != MMLTTB_F64)) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  *variant = stream_variant(d, ydtype);
+  return MMLTTB_OK;
+}
+
+int mmlttb_set_stream_variant(int ydtype, int variant) {
+  if (ydtype != MMLTTB_F32 && ydtype != MMLTTB_F64) return MMLTTB_EINVAL;
+  if (variant < 0 || variant >= kStreamVariants) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  if (d.device < 0 || d.device >= 64) return MMLTTB_EINVAL;
+  g_variant[d.device][ydtype].store(variant);
+  return MMLTTB_OK;
+}
+
+int mmlttb_autotune(int ydtype, const void* y, int64_t n_in, int64_t n_out, int32_t r_ps,
+                    int64_t* out_idx, int64_t out_cap, void* workspace, size_t workspace_bytes,
+                    mmlttb_stream stream, int* best_variant, float* best_ms) {
+  if (!best_variant || (ydtype != MMLTTB_F32 && ydtype != MMLTTB_F64)) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(e);
+  }
+  float best = 3.0e38f;
+  int bv = -1;
+  for (int v = 0; v < kStreamVariants && !rc; ++v) {
+    g_variant_override = v;
+    float t[7];
+    for (int r = 0; r < 3 + 7 && !rc; ++r) {
+      if (r >= 3) {
+        g_ev_start = a;
+        g_ev_stop = b;
+      }
+      rc = run_single(MMLTTB_OP_PRESELECT, y, ydtype, nullptr, MMLTTB_X_IMPLICIT, n_in, n_out, r_ps,
+                      MMLTTB_BINS_INDEX, out_idx, out_cap, nullptr, workspace, workspace_bytes, st);
+      g_ev_start = g_ev_stop = nullptr;
+      if (!rc && r >= 3) {
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) rc = cuda_fail(e);
+        else if ((e = cudaEventElapsedTime(&t[r - 3], a, b)) != cudaSuccess) rc = cuda_fail(e);
+      }
+    }
+    if (rc) break;
+    std::sort(t, t + 7);
+    if (t[3] < best) {
+      best = t[3];
+      bv = v;
+    }
+  }
+  g_variant_override = -1;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if (d.device >= 0 && d.device < 64) g_variant[d.device][ydtype].store(bv);
+  *best_variant = bv;
+  if (best_ms) *best_ms = best;
+  return MMLTTB_OK;
+}
 
 int mmlttb_set_stage_events(void* const* events, int count) {
   if (count < 0 || count > 16 || (count > 0 && !events)) return MMLTTB_EINVAL;

@@ -46,7 +46,8 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
     sp.x = D.xkind == MMLTTB_X_IMPLICIT ? nullptr : D.x;
     sp.ydt = D.ydtype;
     sp.xk = D.xkind;
-    sp.binmode = D.binmode;
+    sp.nan_aware = (D.binmode & MMLTTB_NAN_AWARE) ? 1 : 0;
+    sp.binmode = D.binmode & ~MMLTTB_NAN_AWARE;
     sp.branch = br;
     sp.r_ps = D.r_ps;
     sp.n = D.n_in;
@@ -62,12 +63,14 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
     sp.bincta_off = ctas;
     sp.p0 = br == BR_M4 ? 0 : 1;
     sp.nb = br == BR_M4 ? D.n_in : (D.n_in > 2 ? D.n_in - 2 : 0);
+    // x-width bins can be very uneven: keep whole warps per bin there
+    sp.group = sp.binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(sp.nb, B, D.ydtype == MMLTTB_F32 ? 4 : 8);
     if (mm) {
-      sp.npos = series_work(sp.nb, B);
+      sp.npos = series_work(sp.nb, B, sp.group);
       pos += sp.npos;
       bins += B;
       ctas += (B + kBinsPerCta - 1) / kBinsPerCta;
-      if (D.binmode == MMLTTB_BINS_XWIDTH) edges += B + 1;
+      if (sp.binmode == MMLTTB_BINS_XWIDTH) edges += B + 1;
     }
     if (br == BR_MINMAX_LTTB) {
       b->sel_off[s] = sel;
@@ -95,10 +98,13 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
   b->total_edges = edges;
   b->total_slots = slots;
   b->total_bin_ctas = ctas;
-  b->Wcap = (int64_t)d.sms * d.stream_bps * kStreamWarps;
-  b->W = pos / (kBinCost + 1);  // every warp gets at least one point
-  if (b->W > b->Wcap) b->W = b->Wcap;
-  if (b->W < 1 && pos > 0) b->W = 1;
+  // the variant tuned for the y type that holds most of the batch's points
+  int64_t pts[2] = {0, 0};
+  for (int64_t s = 0; s < n; ++s)
+    if (binned(b->plans[s].branch)) pts[b->plans[s].ydt == MMLTTB_F32 ? 0 : 1] += b->plans[s].nb;
+  b->variant = stream_variant(d, pts[1] > pts[0] ? MMLTTB_F64 : MMLTTB_F32);
+  b->Wcap = stream_warp_cap(d);
+  b->W = stream_warps(d, b->variant, pos);
   if (b->W > 0 && pos / b->W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;
   size_t off = kHeader;
   auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
@@ -205,7 +211,7 @@ int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
   }
   if (b->W > 0) {
     const int64_t grid = (b->W + kStreamWarps - 1) / kStreamWarps;
-    if ((e = launch_stream(bt, grid, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_stream(bt, grid, b->variant, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
   if (b->total_bin_ctas > 0) {

@@ -50,6 +50,8 @@ struct SeriesPlan {
   const void* y;
   const void* x;
   int32_t ydt, xk, binmode, branch, engine, r_ps;
+  int32_t group;     // lanes per bin in the MinMax stream (1..32, a power of two)
+  int32_t nan_aware; // NaN-aware MinMax / M4 (R18)
   int64_t n, n_out;
   int64_t B;         // MinMax bins (minmax branches), else 0
   int64_t p0;        // first binned point: 1 (MinMax over the interior) or 0 (M4)
@@ -165,15 +167,25 @@ __host__ __device__ inline int64_t part_of(int64_t p, int64_t items, int64_t par
 #endif
 }
 
-// Work balance of the MinMax stream.  A bin costs about as much as kBinCost points
-// (its flush is a warp reduction and a record store), so every series occupies
-// D = N + kBinCost*min(B, N) units of a global work space in which interior point q
-// (0-based, q = p-1) sits at unit floor(q*D/N): strictly increasing, steps of at
-// most kBinCost+1.  Warps split the work space evenly, so a warp covering short
-// series with small bins gets fewer points.
-constexpr int64_t kBinCost = 64;
-__host__ __device__ inline int64_t series_work(int64_t N, int64_t B) {
-  return N > 0 ? N + kBinCost * (B < N ? B : N) : 0;
+// Work balance of the MinMax stream.  A bin has a fixed cost (a load round trip and a
+// reduction by its group of lanes), so every series occupies D = N + c*min(B, N)
+// units of a global work space, c = kBinCostPerLane * G, in which binned point q
+// (0-based) sits at unit floor(q*D/N): strictly increasing, steps of at most c+1.
+// Warps split the work space evenly, so a warp covering short series with small
+// bins gets fewer points.
+// A bin handled by a group of G lanes costs about 16*G points of work (a full warp
+// per bin: one load round trip and one reduction per 512 points of float32).
+constexpr int64_t kBinCostPerLane = 16;
+constexpr int64_t kBinCostMax = 32 * kBinCostPerLane;
+__host__ __device__ inline int64_t series_work(int64_t N, int64_t B, int G) {
+  return N > 0 ? N + kBinCostPerLane * G * (B < N ? B : N) : 0;
+}
+// Lanes per bin for a series: about one 16-byte load per lane per bin, a power of two.
+__host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes) {
+  const int64_t per_bin_bytes = (B > 0 ? N / B : N) * elem_bytes;
+  int G = 1;
+  while (G < 32 && (int64_t)G * 64 < per_bin_bytes) G <<= 1;
+  return G;
 }
 
 // Streaming warp w covers global work units [floor(w*T/W), floor((w+1)*T/W)).
@@ -264,7 +276,10 @@ inline cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
   return cudaLaunchKernelEx(&cfg, kernel, bt);
 }
 cudaError_t launch_edges(const Batch& bt, cudaStream_t st);
-cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st);
+// Stream-kernel variants (see stream_variant_info); launch_stream runs one of them.
+constexpr int kStreamVariants = 3;
+cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, cudaStream_t st);
+int stream_variant_info(int variant, int* unroll, int* min_blocks);
 // Compaction (A-2): per-bin resolve, per-series scan of CTA totals, placement.
 cudaError_t launch_compact(const Batch& bt, cudaStream_t st);
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st);
@@ -272,7 +287,7 @@ cudaError_t launch_chain(const Batch& bt, int n_blocks, int64_t max_positions, c
 cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_t st);
 cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st);
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st);
-int stream_blocks_per_sm();
+int stream_blocks_per_sm(int variant);
 int lttb_grid_blocks_per_sm();
 constexpr int kGridThreads = 256;
 

@@ -17,13 +17,20 @@ void stage_mark(cudaStream_t st);
 int cuda_fail(cudaError_t e);
 
 struct DevInfo {
+  int device = 0;
   int sms = 0;
-  int stream_bps = 0;
+  int stream_bps[kStreamVariants] = {};  // resident stream CTAs per SM, per variant
   int grid_bps = 0;
   bool ok = false;
 };
 // SM count and kernel occupancies of the current device (cached per device).
 int get_dev_info(DevInfo* out);
+// Stream variant used for y of type ydt on this device (tuned or default).
+int stream_variant(const DevInfo& d, int ydt);
+// Most streaming warps any variant runs (sizes the record array).
+int64_t stream_warp_cap(const DevInfo& d);
+// Streaming warps of `variant` for `work` units: every warp gets at least one point.
+int64_t stream_warps(const DevInfo& d, int variant, int64_t work);
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kHeader = 256;  // workspace header: status word @0, barrier counter @4, m @8
@@ -41,6 +48,7 @@ struct BatchImpl {
   int64_t n = 0;
   int64_t total_pos = 0, total_bins = 0, total_edges = 0, total_slots = 0;
   int64_t Wcap = 0, W = 0;
+  int variant = 0;
   bool any_block = false;
   int64_t max_tab = 0;  // largest per-series table storage (positions)
   int64_t total_bin_ctas = 0;

@@ -19,14 +19,13 @@ namespace mmlttb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// Build-time tuning of the stream kernel (swept on the target; see the profiles).
-#ifndef MMLTTB_STREAM_UNROLL
-#define MMLTTB_STREAM_UNROLL 4
-#endif
-#ifndef MMLTTB_STREAM_MIN_BLOCKS
-#define MMLTTB_STREAM_MIN_BLOCKS 4
-#endif
-constexpr int kUnroll = MMLTTB_STREAM_UNROLL;  // 16-byte vectors in flight per lane
+// Stream-kernel variants the autotuner chooses from: 16-byte vectors in flight per
+// lane (U) and resident CTAs per SM the register budget is set for (MINB).
+template <int U, int MINB>
+struct StreamCfg {
+  static constexpr int kUnroll = U;
+  static constexpr int kMinBlocks = MINB;
+};
 
 __device__ __forceinline__ float4 ld_stream4(const float4* p) {
   float4 v;
@@ -74,31 +73,36 @@ __device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesP
   return upper_index(bt.edges + sp.edge_off, (int)sp.B, p);
 }
 
-// Warp-wide first-occurrence argmin/argmax of y[lo, hi) for float32 y.
-__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) {
+// First-occurrence argmin/argmax of y[lo, hi) for float32 y by one group of G lanes
+// (gl = lane within the group, gmask = the group's lanes; G = 32: the whole warp).
+// kNanAware: NaN-aware mode (R18): a bin holding a NaN reports its first NaN as both
+// extremes; its record carries the keys LLONG_MIN / LLONG_MAX, which no value has,
+// so merging records keeps the first NaN of the bin.
+template <int kUnroll, bool kNanAware>
+__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
   const uint32_t len = (uint32_t)(hi - lo);
   const float inf = __int_as_float(0x7f800000);
   // Empty state: only strictly smaller (larger) values are recorded, so a lane that
   // sees nothing but +inf (-inf) keeps offset ~0u; if every lane does, the extreme is
   // the first point (offset 0).
   float mn = inf, mx = -inf;
-  uint32_t omn = 0xffffffffu, omx = 0xffffffffu;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
   const uintptr_t aend = ybase + (uintptr_t)hi * 4u;
-  const int64_t nvec = (int64_t)((aend - a0 + 15u) >> 4);
+  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
   const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 4 - lo);  // in [-3, 0]
   const float4* vp = (const float4*)a0;
-  for (int64_t v = lane; v < nvec; v += 32 * kUnroll) {
+  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
     float4 buf[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + 32 * u;
+      int64_t vi = v + G * u;
       if (vi < nvec) buf[u] = ld_stream4(vp + vi);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + 32 * u;
+      int64_t vi = v + G * u;
       if (vi < nvec) {
         const int32_t r = rel0 + 4 * (int32_t)vi;
         const float e[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
@@ -108,6 +112,14 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) 
           const bool ok = (uint32_t)(r + k) < len;
           fm[k] = ok ? e[k] : inf;
           fx[k] = ok ? e[k] : -inf;
+        }
+        if (kNanAware && onan == 0xffffffffu) {
+          const bool any = (e[0] != e[0]) | (e[1] != e[1]) | (e[2] != e[2]) | (e[3] != e[3]);
+          if (any) {
+#pragma unroll
+            for (int k = 3; k >= 0; k--)  // lowest valid NaN of the vector
+              if ((uint32_t)(r + k) < len && e[k] != e[k]) onan = (uint32_t)(r + k);
+          }
         }
         const float m4 = fminf(fminf(fm[0], fm[1]), fminf(fm[2], fm[3]));
         const float x4 = fmaxf(fmaxf(fx[0], fx[1]), fmaxf(fx[2], fx[3]));
@@ -125,15 +137,23 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) 
     }
   }
   const int kmn = key32(mn), kmx = key32(mx);
-  const int wmn = __reduce_min_sync(kFull, kmn);
-  const unsigned wo = __reduce_min_sync(kFull, kmn == wmn ? omn : 0xffffffffu);
-  const int wmx = __reduce_max_sync(kFull, kmx);
-  const unsigned wx = __reduce_min_sync(kFull, kmx == wmx ? omx : 0xffffffffu);
+  const int wmn = __reduce_min_sync(gmask, kmn);
+  const unsigned wo = __reduce_min_sync(gmask, kmn == wmn ? omn : 0xffffffffu);
+  const int wmx = __reduce_max_sync(gmask, kmx);
+  const unsigned wx = __reduce_min_sync(gmask, kmx == wmx ? omx : 0xffffffffu);
   Record r;
   r.kmin = wmn;
   r.kmax = wmx;
   r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
   r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
+  if (kNanAware) {
+    const unsigned wn = __reduce_min_sync(gmask, onan);
+    if (wn != 0xffffffffu) {
+      r.kmin = LLONG_MIN;
+      r.kmax = LLONG_MAX;
+      r.imin = r.imax = lo + (int64_t)wn;
+    }
+  }
   return r;
 }
 
@@ -141,29 +161,30 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int lane) 
 // loop issues no FP64 instruction (FP64 is a narrow pipe on this part): a float
 // compare of the high-word proxies rules out almost every element, and the rest
 // are compared exactly through order-preserving int64 keys.
-__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane) {
+template <int kUnroll, bool kNanAware>
+__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
   const uint32_t len = (uint32_t)(hi - lo);
   // Empty state: keys beyond every double's key and NaN proxies, so the first
   // element a lane sees takes the exact path and is recorded.
   long long kmn = LLONG_MAX, kmx = LLONG_MIN;
   float pmn = __int_as_float(0x7fc00000), pmx = pmn;
-  uint32_t omn = 0xffffffffu, omx = 0xffffffffu;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 8u) & ~(uintptr_t)15;
   const uintptr_t aend = ybase + (uintptr_t)hi * 8u;
-  const int64_t nvec = (int64_t)((aend - a0 + 15u) >> 4);
+  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
   const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 8 - lo);  // in [-1, 0]
   const float inf = __int_as_float(0x7f800000);
-  for (int64_t v = lane; v < nvec; v += 32 * kUnroll) {
+  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
     uint4 buf[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + 32 * u;
+      int64_t vi = v + G * u;
       if (vi < nvec) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u));
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + 32 * u;
+      int64_t vi = v + G * u;
       if (vi < nvec) {
         const int32_t r = rel0 + 2 * (int32_t)vi;
         const bool ok0 = (uint32_t)r < len, ok1 = (uint32_t)(r + 1) < len;
@@ -177,6 +198,11 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane)
           const long long e1 = ((long long)buf[u].w << 32) | buf[u].z;
           const long long k0 = key64(__longlong_as_double(e0));
           const long long k1 = key64(__longlong_as_double(e1));
+          if (kNanAware && onan == 0xffffffffu) {  // NaN proxies always take this path
+            const long long m = 0x7fffffffffffffffLL, inf_bits = 0x7ff0000000000000LL;
+            if (ok1 && (e1 & m) > inf_bits) onan = (uint32_t)(r + 1);
+            if (ok0 && (e0 & m) > inf_bits) onan = (uint32_t)r;
+          }
           if (ok0 && k0 < kmn) { kmn = k0; omn = (uint32_t)r; pmn = p0; }
           if (ok1 && k1 < kmn) { kmn = k1; omn = (uint32_t)(r + 1); pmn = p1; }
           if (ok0 && k0 > kmx) { kmx = k0; omx = (uint32_t)r; pmx = p0; }
@@ -188,21 +214,29 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int lane)
   // int64 order = (signed high word, unsigned low word)
   const int hmn = (int)(kmn >> 32);
   const unsigned lmn = (unsigned)kmn;
-  const int whm = __reduce_min_sync(kFull, hmn);
-  const unsigned wlm = __reduce_min_sync(kFull, hmn == whm ? lmn : 0xffffffffu);
+  const int whm = __reduce_min_sync(gmask, hmn);
+  const unsigned wlm = __reduce_min_sync(gmask, hmn == whm ? lmn : 0xffffffffu);
   const bool eqm = (hmn == whm) && (lmn == wlm);
-  const unsigned wo = __reduce_min_sync(kFull, eqm ? omn : 0xffffffffu);
+  const unsigned wo = __reduce_min_sync(gmask, eqm ? omn : 0xffffffffu);
   const int hmx = (int)(kmx >> 32);
   const unsigned lmx = (unsigned)kmx;
-  const int whx = __reduce_max_sync(kFull, hmx);
-  const unsigned wlx = __reduce_max_sync(kFull, hmx == whx ? lmx : 0u);
+  const int whx = __reduce_max_sync(gmask, hmx);
+  const unsigned wlx = __reduce_max_sync(gmask, hmx == whx ? lmx : 0u);
   const bool eqx = (hmx == whx) && (lmx == wlx);
-  const unsigned wx = __reduce_min_sync(kFull, eqx ? omx : 0xffffffffu);
+  const unsigned wx = __reduce_min_sync(gmask, eqx ? omx : 0xffffffffu);
   Record r;
   r.kmin = ((long long)whm << 32) | wlm;
   r.kmax = ((long long)whx << 32) | wlx;
   r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
   r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
+  if (kNanAware) {
+    const unsigned wn = __reduce_min_sync(gmask, onan);
+    if (wn != 0xffffffffu) {
+      r.kmin = LLONG_MIN;
+      r.kmax = LLONG_MAX;
+      r.imin = r.imax = lo + (int64_t)wn;
+    }
+  }
   return r;
 }
 
@@ -212,26 +246,45 @@ __device__ __forceinline__ int64_t point_at_work(int64_t t, int64_t N, int64_t D
   return muldiv_ceil(t, N, D);
 }
 
-// One warp over the interior points [p_lo, p_hi) of one series.
+// One warp over the binned points [p_lo, p_hi) of one series.  The warp splits into
+// 32/G groups of G lanes (G chosen per series from its mean bin size) and each group
+// works on its own bin, so small bins are processed 32/G at a time.
+template <int kUnroll>
 __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t p_lo,
                                   int64_t p_hi, int64_t w, int lane) {
+  const int G = sp.group;
+  const int ngroups = 32 / G;
+  const int grp = lane / G, gl = lane - grp * G;
+  const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
   int64_t b = bin_containing(bt, sp, p_lo);
   for (;;) {
-    const int64_t sb = bin_start(bt, sp, b);
-    const int64_t sb1 = (b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1);
-    const int64_t lo = sb > p_lo ? sb : p_lo;
-    const int64_t hi = sb1 < p_hi ? sb1 : p_hi;
-    if (lo < hi) {
-      Record r = (sp.ydt == MMLTTB_F32) ? segment_f32((const float*)sp.y, lo, hi, lane)
-                                        : segment_f64((const double*)sp.y, lo, hi, lane);
-      if (lane == 0) bt.rec[sp.bin_off + b + w] = r;
+    const int64_t mb = b + grp;
+    int64_t lo = p_hi, hi = p_hi, sb1 = sp.p0 + sp.nb;
+    if (mb < sp.B) {
+      const int64_t sb = bin_start(bt, sp, mb);
+      sb1 = (mb + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, mb + 1);
+      lo = sb > p_lo ? sb : p_lo;
+      hi = sb1 < p_hi ? sb1 : p_hi;
     }
-    if (sb1 >= p_hi || b + 1 >= sp.B) break;
-    ++b;
+    if (lo < hi) {
+      Record r;
+      if (sp.nan_aware)
+        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G, gmask)
+                                   : segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G, gmask);
+      else
+        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G, gmask)
+                                   : segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G, gmask);
+      if (gl == 0) bt.rec[sp.bin_off + mb + w] = r;
+    }
+    // the round ends with bin b + ngroups - 1 (held by the last group)
+    const int64_t last_end = __shfl_sync(kFull, sb1, 31);
+    if (last_end >= p_hi || b + ngroups >= sp.B) break;
+    b += ngroups;
   }
 }
 
-__global__ void __launch_bounds__(kStreamThreads, MMLTTB_STREAM_MIN_BLOCKS) k_stream(const __grid_constant__ Batch bt) {
+template <int U, int MINB>
+__global__ void __launch_bounds__(kStreamThreads, MINB) k_stream(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31;
@@ -248,7 +301,7 @@ __global__ void __launch_bounds__(kStreamThreads, MMLTTB_STREAM_MIN_BLOCKS) k_st
       // binned points whose work unit lies in [g, seg_end): p0 + q, q in [q_lo, q_hi)
       const int64_t q_lo = point_at_work(g - sp.pos_off, sp.nb, sp.npos);
       const int64_t q_hi = point_at_work(seg_end - sp.pos_off, sp.nb, sp.npos);
-      if (q_hi > q_lo) warp_series_range(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
+      if (q_hi > q_lo) warp_series_range<U>(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
       g = seg_end;
     }
     ++s;
@@ -272,15 +325,25 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
   } else if (b >= sp.B) {
     res = sp.p0 + sp.nb;
   } else {
+    // left edge e_b: int64 x exact (R3); float64 x with every operation rounded (R17)
+    const bool fx = sp.xk == MMLTTB_X_F64;
     const long long* x = (const long long*)sp.x;
-    const long long x0 = __ldg(x), xl = __ldg(x + sp.n - 1);
-    const long long D = xl - x0;
-    const long long eb = x0 + (long long)muldiv(b, D, sp.B);
+    const double* xd = (const double*)sp.x;
+    long long eb = 0;
+    double ebf = 0.0;
+    if (fx) {
+      const double x0 = __ldg(xd), D = __dsub_rn(__ldg(xd + sp.n - 1), x0);
+      ebf = __dadd_rn(x0, __ddiv_rn(__dmul_rn((double)b, D), (double)sp.B));
+    } else {
+      const long long x0 = __ldg(x), xl = __ldg(x + sp.n - 1);
+      eb = x0 + (long long)muldiv(b, xl - x0, sp.B);
+    }
+    auto at_or_after = [&](int64_t q) { return fx ? __ldg(xd + q) >= ebf : __ldg(x + q) >= eb; };
     int64_t lo = sp.p0, hi = sp.p0 + sp.nb;  // answer in [lo, hi]
     while (hi - lo > 32) {
       const int64_t step = (hi - lo + 31) / 32;
       const int64_t q = lo + (int64_t)lane * step;
-      const bool pred = q < hi && __ldg(x + q) >= eb;
+      const bool pred = q < hi && at_or_after(q);
       const unsigned m = __ballot_sync(kFull, pred);
       if (m == 0) {
         const int64_t last = lo + ((hi - lo - 1) / step) * step;  // last sampled point
@@ -293,7 +356,7 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
       }
     }
     const int64_t q = lo + lane;
-    const bool pred = q < hi && __ldg(x + q) >= eb;
+    const bool pred = q < hi && at_or_after(q);
     const unsigned m = __ballot_sync(kFull, pred);
     res = m ? lo + (__ffs(m) - 1) : hi;
   }
@@ -511,9 +574,27 @@ __global__ void __launch_bounds__(kBinsPerCta) k_place(const __grid_constant__ B
 
 }  // namespace
 
-int stream_blocks_per_sm() {
+// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6).
+static const void* stream_kernel(int v) {
+  switch (v) {
+    case 1: return (const void*)k_stream<8, 3>;
+    case 2: return (const void*)k_stream<2, 6>;
+    default: return (const void*)k_stream<4, 4>;
+  }
+}
+
+int stream_variant_info(int v, int* unroll, int* min_blocks) {
+  static const int U[kStreamVariants] = {4, 8, 2}, M[kStreamVariants] = {4, 3, 6};
+  if (v < 0 || v >= kStreamVariants) return -1;
+  *unroll = U[v];
+  *min_blocks = M[v];
+  return 0;
+}
+
+int stream_blocks_per_sm(int v) {
   int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_stream, kStreamThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v), kStreamThreads, 0) !=
+      cudaSuccess)
     return 1;
   return bps > 0 ? bps : 1;
 }
@@ -525,9 +606,14 @@ cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
   return launch_pdl(k_edges, dim3((unsigned)grid), dim3(256), 0, st, bt);
 }
 
-cudaError_t launch_stream(const Batch& bt, int64_t grid, cudaStream_t st) {
+cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, cudaStream_t st) {
   if (bt.n_warps <= 0) return cudaSuccess;
-  return launch_pdl(k_stream, dim3((unsigned)grid), dim3(kStreamThreads), 0, st, bt);
+  const dim3 g((unsigned)grid), b(kStreamThreads);
+  switch (variant) {
+    case 1: return launch_pdl(k_stream<8, 3>, g, b, 0, st, bt);
+    case 2: return launch_pdl(k_stream<2, 6>, g, b, 0, st, bt);
+    default: return launch_pdl(k_stream<4, 4>, g, b, 0, st, bt);
+  }
 }
 
 cudaError_t launch_compact(const Batch& bt, cudaStream_t st) {

@@ -103,7 +103,7 @@ int64_t request_bytes(const Resident& r, const mmlttb_request& q) {
 }
 
 int64_t batch_fixed_bytes(const mmlttb_server* s) {
-  const int64_t wcap = (int64_t)s->dev.sms * s->dev.stream_bps * kStreamWarps;
+  const int64_t wcap = stream_warp_cap(s->dev);
   return (int64_t)kHeader + wcap * (int64_t)sizeof(Record) + 12 * 256;
 }
 
@@ -257,7 +257,7 @@ int validate(const mmlttb_server* s, const mmlttb_request& q) {
   if (q.start < 0 || q.end > r.n || q.start >= q.end) return MMLTTB_EINVAL;
   if (q.n_out < 3 || q.n_out > s->cfg.max_n_out || q.r_ps < 2) return MMLTTB_EINVAL;
   if (q.binmode != MMLTTB_BINS_INDEX && q.binmode != MMLTTB_BINS_XWIDTH) return MMLTTB_EINVAL;
-  if (q.binmode == MMLTTB_BINS_XWIDTH && r.xk != MMLTTB_X_I64) return MMLTTB_EINVAL;
+  if (q.binmode == MMLTTB_BINS_XWIDTH && r.xk == MMLTTB_X_IMPLICIT) return MMLTTB_EINVAL;
   int32_t br;
   int64_t B;
   return classify(MMLTTB_OP_MINMAXLTTB, r.ydt, r.xk, q.end - q.start, q.n_out, q.r_ps, q.binmode, &br, &B);

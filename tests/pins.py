@@ -51,6 +51,19 @@ def bin_members_xwidth(x, B):
     return bins
 
 
+def bin_members_xwidth_f64(x, B, interior=True):
+    """float64 x (R17): e_i = x0 + (i*D)/B with every operation rounded as IEEE
+    doubles (Python floats), point p in the largest bin i with e_i <= x_p."""
+    x = [float(v) for v in x]
+    x0, D = x[0], x[-1] - x[0]
+    edges = [x0 + (float(i) * D) / float(B) for i in range(B)]
+    bins = [[] for _ in range(B)]
+    pts = range(1, len(x) - 1) if interior else range(len(x))
+    for p in pts:
+        bins[max(k for k in range(B) if edges[k] <= x[p])].append(p)
+    return bins
+
+
 def minmax_reference(y, bins):
     """Per bin (argmin, argmax) by numpy (first occurrence), -1 for empty bins."""
     out = []
@@ -175,6 +188,65 @@ def check_minmax_xwidth_bins(o):
                     imin, imax = o.minmax_bins(y, B, x=x, binmode="xwidth")
                     ref = minmax_reference(y, bin_members_xwidth(x, B))
                     assert list(zip(imin.tolist(), imax.tolist())) == ref, (n, B, seed)
+
+
+def check_minmax_xwidth_f64(o):
+    """float64 x with fractional, uneven spacing, repeated values and big gaps."""
+    for seed in range(6):
+        r = rng(900 + seed)
+        for n in (3, 7, 50, 321):
+            g = r.exponential(0.7, n)
+            g[0] = 0.0
+            if seed % 2:
+                g[r.integers(1, n, max(1, n // 5))] = 0.0  # repeated x
+            if n > 4:
+                g[r.integers(1, n)] += 50.0
+            x = np.cumsum(g) - 3.3
+            for y in _series_zoo(seed * 13 + n, n):
+                for B in (1, 2, 5, 17, n + 1):
+                    imin, imax = o.minmax_bins(y, B, x=x, binmode="xwidth")
+                    ref = minmax_reference(y, bin_members_xwidth_f64(x, B))
+                    assert list(zip(imin.tolist(), imax.tolist())) == ref, (n, B, seed)
+                for n_out in (4, 12):
+                    got = o.m4(y, n_out, x=x, binmode="xwidth")
+                    assert list(got) == m4_reference(y, bin_members_xwidth_f64(x, n_out // 4, interior=False))
+        # integer-valued float64 x on a grid: edges fall exactly on points
+        for n in (9, 41, 200):
+            x = np.arange(n, dtype=np.float64) * 2.0 + 1.0
+            y = np.cumsum(r.standard_normal(n))
+            for B in (2, 4, n - 1, (n - 1) // 2):
+                imin, imax = o.minmax_bins(y, B, x=x, binmode="xwidth")
+                assert list(zip(imin.tolist(), imax.tolist())) == minmax_reference(y, bin_members_xwidth_f64(x, B)), (n, B)
+
+
+def _nan_series(r, n, dtype):
+    y = np.cumsum(r.standard_normal(n)).astype(dtype)
+    if n:
+        y[r.integers(0, n, max(1, n // 9))] = np.nan
+    return y
+
+
+def check_nan_aware(o):
+    """NaN-aware MinMax and M4 against numpy argmin/argmax, which return a bin's
+    first NaN when it holds one (R18)."""
+    for seed in range(5):
+        r = rng(950 + seed)
+        for n in (3, 10, 77, 400):
+            for dt in (np.float32, np.float64):
+                y = _nan_series(r, n, dt)
+                for B in (1, 3, 10, n + 2):
+                    imin, imax = o.minmax_bins(y, B, nan_aware=True)
+                    ref = minmax_reference(y, bin_members_index(n, B))
+                    assert list(zip(imin.tolist(), imax.tolist())) == ref, (n, B, seed)
+                for n_out, r_ps in ((3, 2), (10, 4)):
+                    got = o.minmax_preselect(y, n_out, r_ps, nan_aware=True)
+                    assert list(got) == preselect_reference(y, bin_members_index(n, n_out * r_ps // 2))
+                for n_out in (4, 16, 40):
+                    got = o.m4(y, n_out, nan_aware=True)
+                    assert list(got) == m4_reference(y, m4_members_index(n, n_out // 4))
+                x = _increasing_x(r, n, repeats=True)
+                got = o.minmax_preselect(y, 5, 4, x=x, binmode="xwidth", nan_aware=True)
+                assert list(got) == preselect_reference(y, bin_members_xwidth(x, 10))
 
 
 def check_preselect(o):
@@ -380,4 +452,6 @@ ALL_CHECKS = [
     check_symmetries,
     check_constant_series,
     check_m4,
+    check_minmax_xwidth_f64,
+    check_nan_aware,
 ]

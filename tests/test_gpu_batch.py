@@ -38,6 +38,8 @@ def mixed_series(seed, count):
         s = {"y_h": y, "n_out": int(r.choice([3, 4, 10, 57, 200, 1000, 4000])),
              "r_ps": int(r.choice([2, 3, 4, 8])),
              "op": str(r.choice(["minmaxlttb", "minmaxlttb", "lttb", "preselect", "m4"]))}
+        if s["op"] == "m4":
+            s["n_out"] = max(4, s["n_out"])  # M4 takes n_out >= 4
         if s["op"] == "lttb" and n > s["n_out"] and (n - 2) // max(1, s["n_out"] - 2) > 2000:
             s["n_out"] = max(3, n // 1000)  # keep plain-LTTB buckets modest in a batch
         if n >= 3 and r.random() < 0.4:

@@ -273,3 +273,45 @@ def test_m4_xwidth_bins(mm, ref, n, repeats):
     for n_out in (4, 12, 400, 4000):
         eq(mm.m4(dev(y), n_out, x=dev(x), binmode="xwidth"),
            ref.m4(y, n_out, x=x, binmode="xwidth"), f"m4 xwidth n={n} n_out={n_out}")
+
+
+@pytest.mark.parametrize("n", [3, 50, 20011, 100_003])
+def test_xwidth_bins_float64_x(mm, ref, n):
+    """Equal-width bins on float64 x (edges rounded in FP64, R17)."""
+    r = np.random.default_rng(n)
+    g = r.exponential(0.37, n)
+    g[0] = 0.0
+    g[r.integers(1, n, max(1, n // 7))] = 0.0
+    if n > 10:
+        g[r.integers(1, n, 2)] += 1000.0
+    x = np.cumsum(g) - 11.5
+    xg = np.arange(n, dtype=np.float64) * 0.5  # grid: edges land on points
+    for y in (make("walk32", n), make("walk64", n), make("ties32", n)):
+        for xx in (x, xg):
+            for n_out, r_ps in ((3, 2), (40, 4), (1000, 4)):
+                eq(mm.minmax_preselect(dev(y), n_out, r_ps, x=dev(xx), binmode="xwidth"),
+                   ref.minmax_preselect(y, n_out, r_ps, x=xx, binmode="xwidth"), f"f64x preselect n={n}")
+                eq(mm.minmaxlttb(dev(y), n_out, r_ps, x=dev(xx), binmode="xwidth"),
+                   ref.minmaxlttb(y, n_out, r_ps, x=xx, binmode="xwidth"), f"f64x minmaxlttb n={n}")
+            eq(mm.m4(dev(y), 400, x=dev(xx), binmode="xwidth"), ref.m4(y, 400, x=xx, binmode="xwidth"), "f64x m4")
+
+
+@pytest.mark.parametrize("n", [3, 10, 4097, 100_003])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_nan_aware_preselect_and_m4(mm, ref, n, dtype):
+    """NaN-aware MinMax and M4 (R18): a bin holding NaN reports its first NaN."""
+    r = np.random.default_rng(n)
+    y = np.cumsum(r.standard_normal(n)).astype(dtype)
+    y[r.integers(0, n, max(1, n // 50))] = np.nan
+    y[r.integers(0, n, 3)] = np.inf
+    x = increasing_x(n, n + 5, repeats=True)
+    yd, xd = dev(y), dev(x)
+    for n_out, r_ps in ((3, 2), (40, 4), (1000, 4)):
+        eq(mm.minmax_preselect(yd, n_out, r_ps, nan_aware=True),
+           ref.minmax_preselect(y, n_out, r_ps, nan_aware=True), f"nan preselect n={n}")
+        eq(mm.minmax_preselect(yd, n_out, r_ps, x=xd, binmode="xwidth", nan_aware=True),
+           ref.minmax_preselect(y, n_out, r_ps, x=x, binmode="xwidth", nan_aware=True), "nan preselect x")
+    for n_out in (4, 400, 4000):
+        eq(mm.m4(yd, n_out, nan_aware=True), ref.m4(y, n_out, nan_aware=True), f"nan m4 n={n}")
+    with pytest.raises(mm.MMLTTBError):  # NaN-aware is for the aggregations only
+        mm.minmaxlttb(yd, 100, 4, binmode=mm.BINS_INDEX | mm.NAN_AWARE)

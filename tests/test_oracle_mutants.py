@@ -28,20 +28,28 @@ MUTANTS = [
     ("minmax_tie_last_min", "(R8, R10) */\n            if (v < vmin[b])", "(R8, R10) */\n            if (v <= vmin[b])"),
     ("minmax_tie_last_max", "(R8, R10) */\n            if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }\n            if (v > vmax[b])",
      "(R8, R10) */\n            if (v < vmin[b]) { vmin[b] = v; imin[b] = p; }\n            if (v >= vmax[b])"),
-    ("m4_tie_last_min", "last[b] = p;\n            if (v < vmin[b])", "last[b] = p;\n            if (v <= vmin[b])"),
+    ("m4_tie_last_min", "            } else {\n                if (v < vmin[b])", "            } else {\n                if (v <= vmin[b])"),
     ("minmax_includes_first_point", "for (int64_t p = 1; p <= n - 2; p++) {", "for (int64_t p = 0; p <= n - 2; p++) {"),
     ("minmax_includes_last_point", "for (int64_t p = 1; p <= n - 2; p++) {", "for (int64_t p = 1; p <= n - 1; p++) {"),
     ("last_point_dropped", "    out[m++] = n - 1;\n", "\n"),
     ("no_dedupe_equal_extrema", "if (hi != lo) out[m++] = hi;", "out[m++] = hi;"),
-    ("bin_edge_strict", "while (next <= here) {\n            b++;\n            next = NEXT_BOUND(b);",
-     "while (next < here) {\n            b++;\n            next = NEXT_BOUND(b);"),
-    ("m4_bin_edge_strict", "while (next <= here) {\n            b++;\n            next = NEXT_BOUND4(b);",
-     "while (next < here) {\n            b++;\n            next = NEXT_BOUND4(b);"),
+    ("bin_edge_strict", "while (!fx && next <= here) {\n            b++;\n            next = NEXT_BOUND(b);",
+     "while (!fx && next < here) {\n            b++;\n            next = NEXT_BOUND(b);"),
+    ("m4_bin_edge_strict", "while (!fx && next <= here) {\n            b++;\n            next = NEXT_BOUND4(b);",
+     "while (!fx && next < here) {\n            b++;\n            next = NEXT_BOUND4(b);"),
+    ("f64x_edge_strict", "while (nextf <= xf[p]) {\n                b++;\n                nextf = NEXT_EDGE_F(b);",
+     "while (nextf < xf[p]) {\n                b++;\n                nextf = NEXT_EDGE_F(b);"),
+    ("f64x_edge_formula", "#define NEXT_EDGE_F(bb) ((bb) + 1 >= B ? INFINITY : xf0 + ((double)((bb) + 1) * Df) / (double)B)",
+     "#define NEXT_EDGE_F(bb) ((bb) + 1 >= B ? INFINITY : xf0 + ((double)(bb) * Df) / (double)B)"),
     ("bins_from_r_ps_not_halved", "int64_t B = n_out * (int64_t)r_ps / 2;\n    if (B < 1) return MMO_EINVAL;",
      "int64_t B = n_out * (int64_t)r_ps;\n    if (B < 1) return MMO_EINVAL;"),
     ("m4_last_not_updated", "            last[b] = p;\n", "\n"),
-    ("m4_bins_over_interior", "    for (int64_t p = 0; p < n; p++) {\n        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];",
-     "    for (int64_t p = 1; p < n; p++) {\n        __int128 here = binmode == BINS_INDEX ? (__int128)p : (__int128)xi[p];"),
+    ("m4_bins_over_interior", "    for (int64_t p = 0; p < n; p++) {\n        if (fx) {\n            while (nextf <= xf[p]) {\n                b++;\n                nextf = NEXT_EDGE_F4(b);",
+     "    for (int64_t p = 1; p < n; p++) {\n        if (fx) {\n            while (nextf <= xf[p]) {\n                b++;\n                nextf = NEXT_EDGE_F4(b);"),
+    ("nan_last_wins", "        } else if (nan_aware && hasnan[b]) {\n            /* the bin's first NaN decides both extremes (R18) */\n        } else if (nan_aware && isnan(v)) {",
+     "        } else if (nan_aware && isnan(v)) {"),
+    ("nan_ignored", "            hasnan[b] = 1; imin[b] = p; imax[b] = p;\n        } else {\n            /* strict",
+     "            hasnan[b] = 0;\n        } else {\n            /* strict"),
     ("no_lttb_when_rps_covers_n", "if ((int64_t)r_ps * n_out >= n) return mmo_lttb(y, ydt, x, xk, n, n_out, out);", ""),
 ]
 
