@@ -256,8 +256,12 @@ def main():
     kern_avg = sum(kern_ms) / len(kern_ms)
     clk = clocks.summary(t_wall0, t_wall1)
 
-    # per-kernel breakdown of a step (events between the kernels), outside the timed loop
-    names = ["edges", "stream", "merge", "tables", "chain"]
+    # per-kernel breakdown of a step (events between the launch steps), outside the timed loop
+    path = mm.single_path(mm.OP_MINMAXLTTB, mm.F64, mm.X_I64, n, N_OUT, R_PS, mm.BINS_XWIDTH)
+    path_name = {mm.PATH_SPLIT: "split", mm.PATH_FUSED_TAIL: "fused_tail", mm.PATH_FUSED: "fused"}[path]
+    names = {"split": ["edges", "stream", "compaction", "tables", "chain"],
+             "fused_tail": ["edges", "stream", "fused_tail"],
+             "fused": ["fused"]}[path_name]
     st_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(30)]
     for evs in st_ev:
         for ev in evs:
@@ -346,6 +350,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "launch_path": path_name,
         "stage_us_median": stage_us,
         "clocks": clk,
         "parity_vs_oracle": parity,

@@ -69,10 +69,18 @@ def run_1e6(args, mm):
                                         ctypes.c_int64(n_out), ctypes.c_int32(r_ps), 0,
                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_int64(n_out), None,
                                         ctypes.c_void_p(st)), args.steps)
+    paths = {}
+    for name, pid in (("split", mm.PATH_SPLIT), ("fused_tail", mm.PATH_FUSED_TAIL), ("fused", mm.PATH_FUSED)):
+        mm.set_single_path(pid)
+        pm, pb = _time_calls(lambda: mm.minmaxlttb(y, n_out, r_ps, out=out, workspace=ws, sync=False),
+                             args.steps)
+        paths[name] = {"us": pm * 1e3, "us_back_to_back": pb * 1e3}
+    mm.set_single_path(mm.PATH_AUTO)
     _line("MinMaxLTTB latency of one call at n_in=1e6 (device time)", med * 1e3, "us", False,
           {"workload": "single series n_in=1e6 float32 walk, implicit x, n_out=1000, r_ps=4, index bins"},
           {"dtype": "f32", "us_back_to_back": mean * 1e3, "graph_us": gmed * 1e3,
            "graph_us_back_to_back": gmean * 1e3, "noalloc_us": nmed * 1e3,
+           "launch_path": "auto", "by_path": paths,
            "gpts_per_s_back_to_back": n / (mean * 1e-3) / 1e9}, args)
 
 

@@ -322,9 +322,10 @@ int mmlttb_set_timing_events(void *start_event, void *stop_event);
 /*
  * Profiling hook (per calling thread, one shot): the next single-series call
  * records events[0] on its stream before its first kernel and events[k] after its
- * k-th kernel, for as many events as given (at most 16), then forgets them.  For
- * MinMaxLTTB with x-width bins the kernels are: edge search, MinMax stream,
- * compaction, LTTB tables, LTTB chain.
+ * k-th launch step, for as many events as given (at most 16), then forgets them.
+ * For MinMaxLTTB with x-width bins the steps are, on the split path: edge search,
+ * MinMax stream, compaction, LTTB tables, LTTB chain; on the fused-tail path: edge
+ * search, MinMax stream, fused tail; on the fused path: the one fused kernel.
  */
 int mmlttb_set_stage_events(void *const *events, int count);
 
@@ -349,6 +350,35 @@ int mmlttb_set_stream_variant(int ydtype, int variant);
 
 /* Number of kernels this library has launched from the calling thread so far. */
 unsigned long long mmlttb_launch_count(void);
+
+/*
+ * Launch paths of the single-series calls (no counterpart in the paper, which
+ * specifies results, not launches; every path returns the same result).
+ *   MMLTTB_PATH_SPLIT       one grid-wide kernel per step: edge search, MinMax
+ *                           stream, compaction (3 kernels), LTTB tables, LTTB chain.
+ *   MMLTTB_PATH_FUSED_TAIL  edge search and MinMax stream as their own kernels, then
+ *                           ONE persistent kernel (one CTA per SM, cooperative
+ *                           launch) for compaction, tables and chain, with grid-wide
+ *                           barriers between the steps.
+ *   MMLTTB_PATH_FUSED       the whole call as that one persistent kernel (edge
+ *                           search and stream included): the lowest latency for
+ *                           small n.
+ * The barriers wait at most 2 s (then status bit 1, see mmlttb_workspace_status).
+ * AUTO picks FUSED for y of at most 8 MiB, FUSED_TAIL above, and SPLIT where the
+ * fused kernel does not apply (LTTB buckets above 32 points, more than 262144 bins
+ * or 1048576 table positions, or a device where its CTA does not fit).
+ * mmlttb_set_single_path sets a preference for the calling thread (a forced fused
+ * path still falls back to SPLIT where it does not apply); MMLTTB_EINVAL for an
+ * unknown value.  mmlttb_single_path returns the path a call with these arguments
+ * takes on the current device (>= 0), or a negative error code.
+ */
+#define MMLTTB_PATH_AUTO 0
+#define MMLTTB_PATH_SPLIT 1
+#define MMLTTB_PATH_FUSED_TAIL 2
+#define MMLTTB_PATH_FUSED 3
+int mmlttb_set_single_path(int path);
+int mmlttb_single_path(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                       int binmode);
 
 /*
  * Read the workspace's status word (blocking: synchronizes `stream`).  *status

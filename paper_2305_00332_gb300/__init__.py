@@ -21,6 +21,7 @@ X_IMPLICIT, X_I64, X_F64 = 0, 1, 2
 BINS_INDEX, BINS_XWIDTH = 0, 1
 NAN_AWARE = 0x10
 OP_PRESELECT, OP_LTTB, OP_MINMAXLTTB, OP_M4 = 0, 1, 2, 3
+PATH_AUTO, PATH_SPLIT, PATH_FUSED_TAIL, PATH_FUSED = 0, 1, 2, 3
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -349,6 +350,23 @@ def set_stage_events(events):
 def launch_count():
     """Kernels launched by the library from this thread so far."""
     return int(lib.mmlttb_launch_count())
+
+
+lib.mmlttb_set_single_path.argtypes = [_int]
+lib.mmlttb_single_path.argtypes = [_int, _int, _int, _i64, _i64, _i32, _int]
+
+
+def set_single_path(path):
+    """Launch-path preference of this thread's single-series calls (PATH_AUTO,
+    PATH_SPLIT, PATH_FUSED_TAIL or PATH_FUSED)."""
+    _check(lib.mmlttb_set_single_path(path), "mmlttb_set_single_path")
+
+
+def single_path(op, ydtype, xkind, n_in, n_out, r_ps=4, binmode=BINS_INDEX):
+    """The launch path a single-series call with these arguments takes here."""
+    r = lib.mmlttb_single_path(op, ydtype, xkind, n_in, n_out, r_ps, binmode)
+    _check(r if r < 0 else 0, "mmlttb_single_path")
+    return r
 
 
 class SeriesDesc(ctypes.Structure):

@@ -54,6 +54,7 @@ int get_dev_info(DevInfo* out) {
   if (e != cudaSuccess) return cuda_fail(e);
   for (int v = 0; v < kStreamVariants; ++v) d.stream_bps[v] = stream_blocks_per_sm(v);
   d.grid_bps = lttb_grid_blocks_per_sm();
+  d.fused_grid = fused_grid_size(d.sms);
   d.ok = true;
   if (dev >= 0 && dev < 64) g_dev[dev] = d;
   *out = d;
@@ -93,9 +94,11 @@ struct SinglePlan {
   int grid_lttb = 0;
   size_t off_edges = 0, off_rec = 0, off_sel = 0, off_tab = 0, off_means = 0, off_partial = 0;
   size_t off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, off_px = 0, off_py = 0;
+  size_t off_ftot = 0;
   int64_t nct = 0;  // compaction CTAs
   int64_t nb = 0;   // binned points
   int group = 32;   // lanes per bin in the stream
+  int tab_lgS = 0;  // log2 of the fused tables' slots per bucket
   int variant = 0;  // stream-kernel variant
   size_t total = kHeader;
 };
@@ -183,6 +186,8 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     off = align256(off + (size_t)p.nct * 4);
     p.off_ctaoff = off;
     off = align256(off + (size_t)p.nct * 8);
+    p.off_ftot = off;
+    off = align256(off + (size_t)d.sms * 8);
   }
   if (p.branch == BR_MINMAX_LTTB) {
     p.off_sel = off;
@@ -198,6 +203,7 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     p.engine = max_bucket(mcap, p.K) <= kTableMaxBucket ? EN_TABLES : EN_GRID;
     if (p.engine == EN_TABLES) {
       p.tab_cap = mcap;
+      while ((int64_t(1) << p.tab_lgS) < max_bucket(mcap, p.K)) ++p.tab_lgS;
       p.off_tab = off;
       off = align256(off + (size_t)mcap);
     } else {
@@ -211,6 +217,28 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
   p.total = off;
   *P = p;
   return MMLTTB_OK;
+}
+
+// Single-series launch path.  The fused persistent kernel replaces the split
+// compaction/LTTB kernels when the bins and table positions are few enough for its
+// grid; series of up to kFusedStreamBytes of y also run the edge search and the
+// MinMax stream inside it (one launch), larger ones run k_edges/k_stream first.
+constexpr int64_t kFusedMaxBins = int64_t(1) << 18;
+constexpr int64_t kFusedMaxSlots = int64_t(1) << 20;
+constexpr int64_t kFusedStreamBytes = int64_t(8) << 20;
+thread_local int g_path_override = MMLTTB_PATH_AUTO;
+
+int single_path(const SinglePlan& p, const DevInfo& d, int64_t n, int ydt) {
+  if (p.branch == BR_ARANGE || d.fused_grid <= 0 || g_path_override == MMLTTB_PATH_SPLIT)
+    return MMLTTB_PATH_SPLIT;
+  const bool lttb = p.branch == BR_LTTB_ALL || p.branch == BR_MINMAX_LTTB;
+  if (lttb && p.engine != EN_TABLES) return MMLTTB_PATH_SPLIT;
+  if (p.B > kFusedMaxBins || p.tab_cap > kFusedMaxSlots) return MMLTTB_PATH_SPLIT;
+  if (!binned(p.branch)) return MMLTTB_PATH_FUSED_TAIL;  // LTTB on all points: tables + chain
+  if (g_path_override == MMLTTB_PATH_FUSED_TAIL || g_path_override == MMLTTB_PATH_FUSED)
+    return g_path_override;
+  const int64_t bytes = n * (ydt == MMLTTB_F32 ? 4 : 8);
+  return bytes <= kFusedStreamBytes ? MMLTTB_PATH_FUSED : MMLTTB_PATH_FUSED_TAIL;
 }
 
 int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n, int64_t n_out,
@@ -275,8 +303,11 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.means = p.engine == EN_GRID ? (double*)(w + p.off_means) : nullptr;
   sp.out = out;
   sp.out_count = out_count;
+  sp.tab_lgS = p.tab_lgS;
+  set_bin_steps(sp);
   bt.total_pos = p.npos;
   bt.n_warps = p.W;
+  set_warp_divs(bt);
   bt.total_edges = (p.B > 0 && sp.binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
   bt.total_slots = p.tab_cap;
   bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
@@ -287,12 +318,56 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   bt.cta_sum = p.off_ctasum ? (int32_t*)(w + p.off_ctasum) : nullptr;
   bt.cta_series = p.off_ctaser ? (int32_t*)(w + p.off_ctaser) : nullptr;
   bt.cta_off = p.off_ctaoff ? (int64_t*)(w + p.off_ctaoff) : nullptr;
+  bt.fused_tot = p.off_ftot ? (int64_t*)(w + p.off_ftot) : nullptr;
 
-  cudaError_t e = cudaMemsetAsync(ws, 0, kHeader, st);
-  if (e != cudaSuccess) return cuda_fail(e);
   struct StageReset {  // the stage events are one-shot: disarm when this call returns
     ~StageReset() { g_stage_n = g_stage_i = 0; }
   } stage_reset;
+  cudaError_t e;
+  const int path = single_path(p, d, n, ydt);
+  if (path != MMLTTB_PATH_SPLIT) {
+    const int G = d.fused_grid;
+    bt.chain_smem = fused_tab_smem(p.tab_cap);
+    // the header words (status, barrier) are cleared by the first kernel of the
+    // call, or by a memset when the fused kernel is the first
+    const bool lead = path == MMLTTB_PATH_FUSED_TAIL && (bt.total_edges > 0 || p.W > 0);
+    if (!lead && (e = cudaMemsetAsync(ws, 0, kHeader, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
+    if (path == MMLTTB_PATH_FUSED) {
+      int64_t W = p.npos / (kBinCostMax + 1);
+      if (W > fused_warps(G)) W = fused_warps(G);
+      if (W < 1 && p.npos > 0) W = 1;
+      bt.n_warps = W;
+      set_warp_divs(bt);
+      if ((e = launch_fused(bt, G, true, st)) != cudaSuccess) return cuda_fail(e);
+      stage_mark(st);
+      ++g_launches;
+      return MMLTTB_OK;
+    }
+    bt.zero_status = lead ? 1 : 0;  // cleared by the first kernel launched
+    if (bt.total_edges > 0) {
+      if ((e = launch_edges(bt, st)) != cudaSuccess) return cuda_fail(e);
+      stage_mark(st);
+      ++g_launches;
+      bt.zero_status = 0;
+    }
+    if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
+    if (p.W > 0) {
+      const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
+      if ((e = launch_stream(bt, grid, p.variant, st)) != cudaSuccess) return cuda_fail(e);
+      stage_mark(st);
+      ++g_launches;
+      bt.zero_status = 0;
+    }
+    if (g_ev_stop && (e = cudaEventRecord(g_ev_stop, st)) != cudaSuccess) return cuda_fail(e);
+    g_ev_start = g_ev_stop = nullptr;
+    if ((e = launch_fused(bt, G, false, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
+    ++g_launches;
+    return MMLTTB_OK;
+  }
+  e = cudaMemsetAsync(ws, 0, kHeader, st);
+  if (e != cudaSuccess) return cuda_fail(e);
   stage_mark(st);
   if (p.branch == BR_ARANGE) {
     e = launch_iota(out, n, out_count, st);
@@ -558,6 +633,8 @@ int mmlttb_autotune(int ydtype, const void* y, int64_t n_in, int64_t n_out, int3
   }
   float best = 3.0e38f;
   int bv = -1;
+  const int saved_path = g_path_override;
+  g_path_override = MMLTTB_PATH_SPLIT;  // time the stream kernel on its own
   for (int v = 0; v < kStreamVariants && !rc; ++v) {
     g_variant_override = v;
     float t[7];
@@ -582,6 +659,7 @@ int mmlttb_autotune(int ydtype, const void* y, int64_t n_in, int64_t n_out, int3
     }
   }
   g_variant_override = -1;
+  g_path_override = saved_path;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;
@@ -606,6 +684,23 @@ int mmlttb_set_timing_events(void* start_event, void* stop_event) {
 }
 
 unsigned long long mmlttb_launch_count(void) { return g_launches; }
+
+int mmlttb_set_single_path(int path) {
+  if (path < MMLTTB_PATH_AUTO || path > MMLTTB_PATH_FUSED) return MMLTTB_EINVAL;
+  g_path_override = path;
+  return MMLTTB_OK;
+}
+
+int mmlttb_single_path(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                       int binmode) {
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(op, ydtype, xkind, n_in, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  return single_path(p, d, n_in, ydtype);
+}
 
 int mmlttb_workspace_status(const void* workspace, int* status, mmlttb_stream stream) {
   if (!workspace || !status) return MMLTTB_EINVAL;

@@ -72,6 +72,7 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
       ctas += (B + kBinsPerCta - 1) / kBinsPerCta;
       if (sp.binmode == MMLTTB_BINS_XWIDTH) edges += B + 1;
     }
+    set_bin_steps(sp);
     if (br == BR_MINMAX_LTTB) {
       b->sel_off[s] = sel;
       sel += 2 * B + 2;
@@ -186,6 +187,7 @@ static Batch batch_args(const BatchImpl* b, void* ws) {
   bt.n_series = (int32_t)b->n;
   bt.total_pos = b->total_pos;
   bt.n_warps = b->W;
+  set_warp_divs(bt);
   bt.total_edges = b->total_edges;
   bt.total_slots = b->total_slots;
   bt.rec = (Record*)(w + b->off_rec);

@@ -31,13 +31,49 @@ enum Engine : int32_t {
   EN_BLOCK = 3,   // one CTA per series, one block-wide step per bucket
 };
 
+constexpr unsigned kFull = 0xffffffffu;
+
 // Largest LTTB bucket (in points) the transition-table engine accepts.
 constexpr int kTableMaxBucket = 32;
+// Shared memory that m table bytes take when staged for the chain: one 4-byte pad
+// word after every 32 bytes (bank spread), rounded up to 16 bytes.
+__host__ __device__ inline int64_t staged_tab_bytes(int64_t m) {
+  const int64_t w = (m + 3) / 4;
+  return ((w + (w + 7) / 8) * 4 + 15) & ~int64_t(15);
+}
 // Bins per CTA of the compaction kernels; every series' bins start on a CTA boundary.
 constexpr int kBinsPerCta = 256;
 // Threads of the streaming MinMax kernel's CTAs.
 constexpr int kStreamThreads = 256;
 constexpr int kStreamWarps = kStreamThreads / 32;
+
+// Division by a divisor fixed ahead of the kernel (bins, points, work units, warps,
+// buckets).  An integer division costs hundreds of cycles of latency on this part;
+// with inv = floor((2^64-1)/d), computed once where d is set (on the host),
+// umulhi(a, inv) is floor(a/d) or one less, and one compare fixes it.
+struct Div {
+  uint64_t d = 1, inv = ~0ull;
+};
+__host__ __device__ inline Div make_div(int64_t d) {
+  Div r;
+  r.d = d > 0 ? (uint64_t)d : 1ull;
+  r.inv = ~0ull / r.d;
+  return r;
+}
+__host__ __device__ inline uint64_t div_by(uint64_t a, const Div& D) {
+#ifdef __CUDA_ARCH__
+  uint64_t q = __umul64hi(a, D.inv);
+  uint64_t r = a - q * D.d;
+  if (r >= D.d) {
+    ++q;
+    r -= D.d;
+  }
+  if (r >= D.d) ++q;
+  return q;
+#else
+  return a / D.d;
+#endif
+}
 
 // Result of one warp over one bin (or the part of a bin inside the warp's range):
 // order-preserving integer keys of the extreme y values and their point indices.
@@ -51,6 +87,10 @@ struct SeriesPlan {
   const void* x;
   int32_t ydt, xk, binmode, branch, engine, r_ps;
   int32_t group;     // lanes per bin in the MinMax stream (1..32, a power of two)
+  int32_t bin_r1, bin_rs;  // index bins: nb mod B and (32/group)*nb mod B (set_bin_steps)
+  int64_t bin_q1, bin_qs;  // index bins: floor(nb/B) and floor((32/group)*nb/B)
+  Div dB, dnb, dnpos, dK;  // divisors B, nb, npos and K = n_out - 2 (set_bin_steps)
+  int32_t tab_lgS;         // fused tables: log2 of the slots per bucket (>= largest bucket)
   int32_t nan_aware; // NaN-aware MinMax / M4 (R18)
   int64_t n, n_out;
   int64_t B;         // MinMax bins (minmax branches), else 0
@@ -83,6 +123,7 @@ struct Batch {
   int32_t n_series;
   int64_t total_pos;   // sum of npos: the total work the streaming warps split evenly
   int64_t n_warps;     // streaming warps, each with at least one interior point
+  Div dtotal, dwarps;  // divisors total_pos and n_warps (set_warp_divs)
   int64_t total_edges; // sum over x-width series of B+1
   int64_t total_slots; // sum of tab_cap
   int64_t total_bin_ctas;  // compaction CTAs over all minmax series
@@ -93,10 +134,33 @@ struct Batch {
   int32_t* cta_series; // per compaction CTA: its series
   int64_t* cta_off;    // per compaction CTA: exclusive prefix of cta_sum within its series
   unsigned* status;    // error bits (1: a bounded wait timed out, 2: device check failed)
-  unsigned* barrier;   // grid barrier counter (EN_GRID)
+  unsigned* barrier;   // grid barrier counter (EN_GRID and the fused kernel)
+  int64_t* fused_tot;  // per CTA of the fused kernel: indices its bins emit
   double* partial;     // 2 x grid x (area, position) partials (EN_GRID)
   int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
+  int32_t zero_status; // the launch clears the status and barrier words first (first kernel of a call)
 };
+
+__host__ __device__ inline void set_bin_steps(SeriesPlan& sp) {
+  sp.dB = make_div(sp.B);
+  sp.dnb = make_div(sp.nb);
+  sp.dnpos = make_div(sp.npos);
+  sp.dK = make_div(sp.n_out - 2);
+  sp.bin_q1 = sp.bin_qs = 0;
+  sp.bin_r1 = sp.bin_rs = 0;
+  if (sp.B <= 0 || sp.nb < 0 || sp.group <= 0) return;
+  const int64_t s = 32 / sp.group;
+  sp.bin_q1 = sp.nb / sp.B;
+  sp.bin_r1 = (int32_t)(sp.nb - sp.bin_q1 * sp.B);
+  sp.bin_qs = (s * sp.nb) / sp.B;
+  sp.bin_rs = (int32_t)(s * sp.nb - sp.bin_qs * sp.B);
+}
+
+// Divisors of the stream's warp partition, after total_pos and n_warps are set.
+__host__ __device__ inline void set_warp_divs(Batch& bt) {
+  bt.dtotal = make_div(bt.total_pos);
+  bt.dwarps = make_div(bt.n_warps);
+}
 
 __host__ __device__ inline const SeriesPlan& plan_of(const Batch& bt, int s) {
   return bt.plans ? bt.plans[s] : bt.one;
@@ -167,6 +231,76 @@ __host__ __device__ inline int64_t part_of(int64_t p, int64_t items, int64_t par
 #endif
 }
 
+// The same with a prepared divisor (the fast path when the product fits 64 bits).
+__host__ __device__ inline int64_t muldiv(int64_t a, int64_t b, const Div& c) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  const unsigned long long hi = __umul64hi((unsigned long long)a, (unsigned long long)b);
+  if (hi == 0) return (int64_t)div_by(lo, c);
+  const unsigned __int128 num = ((unsigned __int128)hi << 64) | lo;
+  return (int64_t)(num / c.d);
+#else
+  return muldiv(a, b, (int64_t)c.d);
+#endif
+}
+__host__ __device__ inline int64_t muldiv_ceil(int64_t a, int64_t b, const Div& c) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  const unsigned long long hi = __umul64hi((unsigned long long)a, (unsigned long long)b);
+  if (hi == 0) {
+    const unsigned long long q = div_by(lo, c);
+    return (int64_t)(q + (q * c.d != lo ? 1 : 0));
+  }
+  return muldiv_ceil(a, b, (int64_t)c.d);
+#else
+  return muldiv_ceil(a, b, (int64_t)c.d);
+#endif
+}
+__host__ __device__ inline int64_t part_start(int64_t j, int64_t items, const Div& parts) {
+  return muldiv(j, items, parts) + 1;
+}
+__host__ __device__ inline int64_t part_of(int64_t p, const Div& items, int64_t parts) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long lo = (unsigned long long)p * (unsigned long long)parts;
+  const unsigned long long hi = __umul64hi((unsigned long long)p, (unsigned long long)parts);
+  if (hi == 0) return (int64_t)div_by(lo - 1ull, items);
+  return part_of(p, (int64_t)items.d, parts);
+#else
+  return part_of(p, (int64_t)items.d, parts);
+#endif
+}
+
+// floor(j*N/K) for j = j0, j0 + s, j0 + 2s, ... (N >= 0, K >= 1, s*N < 2^63) with
+// no division per step: an integer division costs hundreds of cycles of latency on
+// this part, a step a few adds.
+struct StepDiv {
+  int64_t L = 0, rem = 0;   // floor(j*N/K) and j*N - L*K, in [0, K)
+  int64_t qs = 0, rs = 0;   // floor(s*N/K) and s*N - qs*K
+  int64_t K = 1;
+  __host__ __device__ void init(int64_t j, int64_t N, const Div& dK, int64_t s) {
+    K = (int64_t)dK.d;
+    L = muldiv(j, N, dK);
+    // the true remainder lies in [0, K): exact in wrapping 64-bit arithmetic
+    rem = (int64_t)((uint64_t)j * (uint64_t)N - (uint64_t)L * (uint64_t)K);
+    qs = (int64_t)div_by((uint64_t)(s * N), dK);
+    rs = s * N - qs * K;
+  }
+  __host__ __device__ void next() {  // j -> j + s
+    L += qs;
+    rem += rs;
+    if (rem >= K) {
+      rem -= K;
+      L += 1;
+    }
+  }
+};
+
+// Index-bin step constants of a plan (after nb, B and group are set): a lane group of
+// the stream moves from bin mb to mb + 32/group per round and needs bin starts
+// floor(mb*nb/B) without a division per round.
+struct SeriesPlan;
+__host__ __device__ inline void set_bin_steps(SeriesPlan& sp);
+
 // Work balance of the MinMax stream.  A bin has a fixed cost (a load round trip and a
 // reduction by its group of lanes), so every series occupies D = N + c*min(B, N)
 // units of a global work space, c = kBinCostPerLane * G, in which binned point q
@@ -189,11 +323,11 @@ __host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes
 }
 
 // Streaming warp w covers global work units [floor(w*T/W), floor((w+1)*T/W)).
-__host__ __device__ inline int64_t warp_begin(int64_t w, int64_t total, int64_t warps) {
+__host__ __device__ inline int64_t warp_begin(int64_t w, int64_t total, const Div& warps) {
   return muldiv(w, total, warps);
 }
 // The warp whose range holds global work unit g: floor(((g+1)*W - 1) / T).
-__host__ __device__ inline int64_t warp_of(int64_t g, int64_t total, int64_t warps) {
+__host__ __device__ inline int64_t warp_of(int64_t g, const Div& total, int64_t warps) {
   return part_of(g + 1, total, warps);
 }
 
@@ -288,6 +422,20 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_
 cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st);
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st);
 int stream_blocks_per_sm(int variant);
+// Fused single-series kernel, one CTA per SM (fused.cu): its grid on a device with
+// `sms` SMs (0 when it does not fit), the dynamic shared memory it stages tables in,
+// its streaming warps, and the launch (with or without the edge search and the
+// MinMax stream).
+int fused_grid_size(int sms);
+int64_t fused_tab_smem(int64_t tab_cap);
+int fused_warps(int grid);
+cudaError_t launch_fused(const Batch& bt, int grid, bool with_stream, cudaStream_t st);
+// Clear the workspace header words a call's kernels use (status word and barrier
+// counter); run by the first kernel of a call that has no header memset.
+__device__ __forceinline__ void zero_header(const Batch& bt) {
+  *bt.status = 0u;
+  *bt.barrier = 0u;
+}
 int lttb_grid_blocks_per_sm();
 constexpr int kGridThreads = 256;
 

@@ -21,6 +21,7 @@ struct DevInfo {
   int sms = 0;
   int stream_bps[kStreamVariants] = {};  // resident stream CTAs per SM, per variant
   int grid_bps = 0;
+  int fused_grid = 0;  // CTAs of the fused single-series kernel (0: unavailable)
   bool ok = false;
 };
 // SM count and kernel occupancies of the current device (cached per device).

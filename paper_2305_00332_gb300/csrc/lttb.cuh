@@ -1,0 +1,442 @@
+// Device code of the LTTB step (Sec. 2.2.1 LTTB; Sec. 3 second step of MinMaxLTTB)
+// on small buckets, shared by the split kernels (k_tables, k_chain) and the fused
+// single-cluster kernel.
+//
+// LTTB is a chain: the pick b_j of bucket j depends on the pick of bucket j-1.  When
+// buckets are small (MinMaxLTTB puts about r_ps points in each), the chain is cut
+// into independent pieces:
+//   table_entry    every position p that can be the previous pick of bucket j (p in
+//                  bucket j-1, or p = 0 for j = 0) gets T[p] = the offset in bucket j
+//                  of the point with the largest area against p and the mean of
+//                  bucket j+1.  Each area is the same FP64 expression the sequential
+//                  method evaluates, so every entry equals the sequential choice for p.
+//   chain_series   one CTA resolves b_j = T[L_{j-1} + b_{j-1}] for all j by a
+//                  parallel prefix over function composition (Hillis-Steele), then
+//                  writes the picked indices.
+#pragma once
+
+#include "common.cuh"
+
+namespace mmlttb {
+namespace {
+
+__device__ __forceinline__ int64_t lttb_m(const SeriesPlan& sp) {
+  return sp.branch == BR_LTTB_ALL ? sp.n : *sp.m_ptr;
+}
+
+// Mean of LTTB positions [lo, hi): left-to-right FP64 sums, one division each (R7).
+__device__ void bucket_mean(const SeriesPlan& sp, int64_t lo, int64_t hi, double* xc, double* yc) {
+  double sx = 0.0, sy = 0.0;
+  if (sp.xk == MMLTTB_X_IMPLICIT && !sp.sel && hi > 0 && hi - lo <= ((1ll << 53) - 1) / hi) {
+    // Implicit x on all points: the indices lo..hi-1 and all their partial sums are
+    // integers below 2^53, so the sequential FP64 sum is exact and equals the
+    // closed form.
+    sx = (double)((lo + hi - 1) * (hi - lo) / 2);
+    for (int64_t p = lo; p < hi; p += 4) {
+      double yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) yv[u] = p + u < hi ? y_of(sp, p + u) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (p + u < hi) sy = __dadd_rn(sy, yv[u]);
+    }
+  } else {
+    // four points' loads in flight, then the sums in order (left to right)
+    for (int64_t p = lo; p < hi; p += 4) {
+      double xv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xv[u] = yv[u] = 0.0;
+        if (p + u < hi) pos_xy(sp, p + u, &xv[u], &yv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (p + u < hi) {
+          sx = __dadd_rn(sx, xv[u]);
+          sy = __dadd_rn(sy, yv[u]);
+        }
+    }
+  }
+  const double cnt = (double)(hi - lo);
+  *xc = __ddiv_rn(sx, cnt);
+  *yc = __ddiv_rn(sy, cnt);
+}
+
+// Bounds of the bucket after bucket j (R1), or the last point for the last bucket (R5).
+__device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N, int64_t m,
+                                            int64_t* lo, int64_t* hi) {
+  if (j + 1 < (int64_t)dK.d) {
+    *lo = part_start(j + 1, N, dK);
+    *hi = part_start(j + 2, N, dK);
+  } else {
+    *lo = m - 1;
+    *hi = m;
+  }
+}
+
+// Table entry of slot `slot` of the launch's table-slot space.  Warp-collective: all
+// 32 lanes call it together (lanes without an entry pass any slot; they only take
+// part in the shared-mean exchange).  Lanes that target the same bucket of the same
+// series share its next-bucket mean: the lowest such lane computes it (R7).
+__device__ void table_entry(const Batch& bt, int64_t slot, int lane) {
+  bool work = slot < bt.total_slots;
+  int s = 0;
+  int64_t p = 0, m = 0, K = 0, N = 0, jt = 0;
+  const SeriesPlan* spp = nullptr;
+  if (work) {
+    s = bt.tab_offs ? upper_index(bt.tab_offs, bt.n_series, slot) : 0;
+    spp = &plan_of(bt, s);
+    p = slot - spp->tab_off;
+    work = spp->engine == EN_TABLES;
+    if (work) {
+      m = lttb_m(*spp);
+      work = p < m && m > spp->n_out;
+    }
+    if (work) {
+      K = spp->n_out - 2;
+      N = m - 2;
+      if (p == 0) jt = 0;               // the bucket whose pick follows a pick at p
+      else if (p <= m - 2) jt = part_of(p, N, K) + 1;
+      else work = false;
+      if (jt >= K) work = false;
+    }
+  }
+  const unsigned long long key = work ? ((unsigned long long)s << 40) ^ (unsigned long long)jt
+                                      : ~0ull - (unsigned long long)lane;
+  const unsigned group = __match_any_sync(kFull, key);
+  const int leader = __ffs(group) - 1;
+  double xc = 0.0, yc = 0.0, xa = 0.0, ya = 0.0;
+  double xb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t lo = 0, hi = 0;
+  if (work) {
+    const SeriesPlan& sp = *spp;
+    pos_xy(sp, p, &xa, &ya);
+    // bucket jt = [lo, hi) (R1) and the next one, stepped from one division
+    StepDiv bs;
+    bs.init(jt, N, sp.dK, 1);
+    lo = bs.L + 1;
+    bs.next();
+    hi = bs.L + 1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)  // the first candidates load while the mean is formed
+      if (lo + u < hi) pos_xy(sp, lo + u, &xb[u], &yb[u]);
+    if (lane == leader) {
+      int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point (R5)
+      if (jt + 1 < K) {
+        nlo = hi;
+        bs.next();
+        nhi = bs.L + 1;
+      }
+      bucket_mean(sp, nlo, nhi, &xc, &yc);
+    }
+  }
+  xc = __shfl_sync(kFull, xc, leader);
+  yc = __shfl_sync(kFull, yc, leader);
+  if (!work) return;
+  const SeriesPlan& sp = *spp;
+  long long best = -1;  // bits of a non-negative double order like the double
+  int pick = 0;
+  for (int64_t q0 = lo; q0 < hi; q0 += 4) {  // four candidates' loads in flight
+    if (q0 > lo) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < hi) pos_xy(sp, q0 + u, &xb[u], &yb[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (q0 + u >= hi) break;
+      const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], xc, yc));
+      if (q0 + u == lo || ab > best) {  // R8: the first largest wins
+        best = ab;
+        pick = (int)(q0 + u - lo);
+      }
+    }
+  }
+  sp.tab[p] = (uint8_t)pick;
+}
+
+// Table entries of one series laid out bucket-major: slot j*S + k (S = 2^tab_lgS,
+// at least the largest bucket) is the entry of the k-th position of bucket j-1 (of
+// position 0 for j = 0), which picks in bucket j.  Warp-collective (all 32 lanes,
+// S lanes per bucket).  The bucket follows from the slot by a shift and the bucket
+// starts step from one floor(j*N/K), so nothing divides by the position count; the
+// first lane of a bucket forms the mean of bucket j+1 (R7) for all S lanes.
+__device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot, int lane) {
+  const int lgS = sp.tab_lgS, S = 1 << lgS;
+  const int64_t K = sp.n_out - 2, N = m - 2;
+  const int64_t j = slot >> lgS;
+  const int k = (int)(slot & (S - 1));
+  bool work = false;
+  int64_t p = 0, lo = 0, hi = 0;
+  double xc = 0.0, yc = 0.0, xa = 0.0, ya = 0.0;
+  double xb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < K) {
+    StepDiv bs;
+    int64_t lprev = 0;
+    if (j == 0) {
+      bs.init(0, N, sp.dK, 1);
+    } else {
+      bs.init(j - 1, N, sp.dK, 1);
+      lprev = bs.L + 1;  // start of bucket j-1
+      bs.next();
+    }
+    lo = bs.L + 1;  // bucket j = [lo, hi) (R1)
+    bs.next();
+    hi = bs.L + 1;
+    p = j == 0 ? 0 : lprev + k;
+    work = k < (j == 0 ? 1 : lo - lprev);
+    if (work) {
+      pos_xy(sp, p, &xa, &ya);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)  // the first candidates load while the mean is formed
+        if (lo + u < hi) pos_xy(sp, lo + u, &xb[u], &yb[u]);
+    }
+    if (k == 0) {
+      int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point (R5)
+      if (j + 1 < K) {
+        nlo = hi;
+        bs.next();
+        nhi = bs.L + 1;
+      }
+      bucket_mean(sp, nlo, nhi, &xc, &yc);
+    }
+  }
+  const int leader = lane & ~(S - 1);
+  xc = __shfl_sync(kFull, xc, leader);
+  yc = __shfl_sync(kFull, yc, leader);
+  if (!work) return;
+  long long best = -1;  // bits of a non-negative double order like the double
+  int pick = 0;
+  for (int64_t q0 = lo; q0 < hi; q0 += 4) {
+    if (q0 > lo) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < hi) pos_xy(sp, q0 + u, &xb[u], &yb[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (q0 + u >= hi) break;
+      const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], xc, yc));
+      if (q0 + u == lo || ab > best) {  // R8: the first largest wins
+        best = ab;
+        pick = (int)(q0 + u - lo);
+      }
+    }
+  }
+  sp.tab[p] = (uint8_t)pick;
+}
+
+// Bucket starts L_j = floor(j*N/K)+1 for consecutive j without a division per step.
+struct PartIter {
+  StepDiv sd;
+  int64_t L = 0;
+  __device__ PartIter() {}
+  __device__ PartIter(int64_t j, int64_t N, const Div& dK) {
+    sd.init(j, N, dK, 1);
+    L = sd.L + 1;
+  }
+  __device__ void next() {  // j -> j+1
+    sd.next();
+    L = sd.L + 1;
+  }
+};
+
+// A map of at most 8 entries with values below 8, one byte per entry (entry i in
+// byte i of {hi:lo}), so that composing two maps is two byte permutations.
+struct Map8 {
+  unsigned lo, hi;
+};
+// Selector nibbles for __byte_perm from four bytes (each below 8).
+__device__ __forceinline__ unsigned nibbles(unsigned w) {
+  return (w & 0x7u) | ((w >> 4) & 0x70u) | ((w >> 8) & 0x700u) | ((w >> 12) & 0x7000u);
+}
+// (a after b)(i) = a[b[i]]
+__device__ __forceinline__ Map8 compose(Map8 a, Map8 b) {
+  return {__byte_perm(a.lo, a.hi, nibbles(b.lo)), __byte_perm(a.lo, a.hi, nibbles(b.hi))};
+}
+__device__ __forceinline__ int map_at(Map8 a, int i) {
+  return (int)(((i < 4 ? a.lo : a.hi) >> (8 * (i & 3))) & 0xffu);
+}
+__device__ __forceinline__ Map8 shfl_up_map(Map8 a, int d) {
+  return {__shfl_up_sync(kFull, a.lo, d), __shfl_up_sync(kFull, a.hi, d)};
+}
+
+// The LTTB output of series sp once its tables are written.  Block-collective over
+// NT threads.  F ([2][kTableMaxBucket][NT]) and dom ([2][NT]) are shared scratch;
+// s_tab4 holds up to tab_smem bytes of shared memory for staging the tables
+// (staged_tab_bytes(m) of them when they fit).
+//   Phase 1: thread t composes the steps of its segment of buckets [j0, j1) for
+//            every entry offset in bucket j0-1 (four entries at a time, so four
+//            independent table loads are in flight).
+//   Phase 2: the prefix of the segment maps under composition, evaluated at the
+//            chain's start (position 0): with buckets of at most 8 positions the
+//            maps live in registers (warp shuffle scan, then one pass over the
+//            warps' totals); otherwise a Hillis-Steele scan over shared memory.
+//   Phase 3: each segment is walked from its resolved entry, writing positions;
+//            then positions become indices with independent loads.
+template <int NT>
+__device__ void chain_series(const SeriesPlan& sp, uint4* s_tab4, int64_t tab_smem,
+                             uint8_t (*F)[kTableMaxBucket][NT], uint8_t (*dom)[NT]) {
+  __shared__ unsigned s_wlo[NT / 32], s_whi[NT / 32];
+  __shared__ int s_went[NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (sp.branch == BR_ARANGE) {
+    for (int64_t i = tid; i < sp.n; i += NT) sp.out[i] = i;
+    if (tid == 0 && sp.out_count) *sp.out_count = sp.n;
+    return;
+  }
+  if (sp.branch != BR_LTTB_ALL && sp.branch != BR_MINMAX_LTTB) return;
+  const int64_t m = lttb_m(sp);
+  if (m <= sp.n_out) {  // nothing to drop (R14)
+    for (int64_t i = tid; i < m; i += NT) sp.out[i] = index_of(sp, i);
+    if (tid == 0 && sp.out_count) *sp.out_count = m;
+    return;
+  }
+  if (sp.engine != EN_TABLES) return;
+  const int64_t K = sp.n_out - 2, N = m - 2;
+  const int T = K < NT ? (int)K : NT;
+  const bool packed = (N + K - 1) / K <= 8;  // every bucket holds at most 8 positions
+  // Staged tables keep byte q at q + 4*(q/32): the threads walk segments about 32
+  // positions apart, and without the pad word per 32 bytes a warp's lookups would
+  // fall into 4 of the 32 banks.
+  const uint8_t* tab = sp.tab;
+  int64_t padw = 0;
+  if (staged_tab_bytes(m) <= tab_smem) {
+    const int64_t nw4 = (m + 3) / 4;  // 4-byte words (the storage is padded to 16 bytes)
+    const unsigned* src = (const unsigned*)sp.tab;
+    unsigned* dst = (unsigned*)s_tab4;
+    for (int64_t i0 = tid; i0 < nw4; i0 += 4 * NT) {  // four L2 loads in flight per thread
+      unsigned w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = i0 + u * NT < nw4 ? __ldcg(src + i0 + u * NT) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * NT;
+        if (i < nw4) dst[i + (i >> 3)] = w[u];
+      }
+    }
+    __syncthreads();
+    tab = (const uint8_t*)s_tab4;
+    padw = 4;
+  }
+  static_assert((NT & (NT - 1)) == 0, "NT must be a power of two");
+  int64_t j0 = 0, j1 = 0;
+  Map8 P = {0x03020100u, 0x07060504u};  // identity (threads without a segment keep it)
+  PartIter it0;
+  int64_t l0 = 0;
+  if (tid < T) {
+    // segment [floor(t*K/T), floor((t+1)*K/T)): T = NT (a power of two) or T = K
+    if (T == NT) {
+      j0 = (int64_t)(((uint64_t)tid * (uint64_t)K) / (uint64_t)NT);
+      j1 = (int64_t)(((uint64_t)(tid + 1) * (uint64_t)K) / (uint64_t)NT);
+    } else {
+      j0 = tid;
+      j1 = tid + 1;
+    }
+    it0 = PartIter(j0 > 0 ? j0 - 1 : 0, N, sp.dK);  // start of bucket j0-1 (or of bucket 0)
+    int d0 = 1;
+    if (j0 > 0) {
+      l0 = it0.L;
+      it0.next();
+      d0 = (int)(it0.L - l0);
+    }
+    for (int ia = 0; ia < d0; ia += 4) {
+      int v0 = ia, v1 = ia + 1 < d0 ? ia + 1 : ia, v2 = ia + 2 < d0 ? ia + 2 : ia;
+      int v3 = ia + 3 < d0 ? ia + 3 : ia;
+      PartIter it = it0;
+      int64_t lprev = l0;
+      for (int64_t j = j0; j < j1; ++j) {
+        v0 = tab[lprev + v0 + (((lprev + v0) >> 5) * padw)];
+        v1 = tab[lprev + v1 + (((lprev + v1) >> 5) * padw)];
+        v2 = tab[lprev + v2 + (((lprev + v2) >> 5) * padw)];
+        v3 = tab[lprev + v3 + (((lprev + v3) >> 5) * padw)];
+        lprev = it.L;  // start of bucket j
+        it.next();
+      }
+      if (packed) {
+        const unsigned w = (unsigned)v0 | ((unsigned)v1 << 8) | ((unsigned)v2 << 16) | ((unsigned)v3 << 24);
+        if (ia == 0) P.lo = w; else P.hi = w;
+      } else {
+        F[0][ia][tid] = (uint8_t)v0;
+        if (ia + 1 < d0) F[0][ia + 1][tid] = (uint8_t)v1;
+        if (ia + 2 < d0) F[0][ia + 2][tid] = (uint8_t)v2;
+        if (ia + 3 < d0) F[0][ia + 3][tid] = (uint8_t)v3;
+      }
+    }
+    if (!packed) dom[0][tid] = (uint8_t)d0;
+  }
+  int v;  // entry offset of this thread's segment (in bucket j0-1)
+  if (packed) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const Map8 o = shfl_up_map(P, d);
+      if (lane >= d) P = compose(P, o);
+    }
+    // P: this warp's segments up to and including this thread's, composed
+    if (lane == 31) {
+      s_wlo[wid] = P.lo;
+      s_whi[wid] = P.hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int e = 0;  // the chain starts at position 0
+      for (int w = 0; w < NT / 32; ++w) {
+        s_went[w] = e;
+        e = map_at(Map8{s_wlo[w], s_whi[w]}, e);
+      }
+    }
+    __syncthreads();
+    const Map8 prev = shfl_up_map(P, 1);
+    v = lane == 0 ? s_went[wid] : map_at(prev, s_went[wid]);
+  } else {
+    int c = 0;
+    for (int d = 1; d < T; d <<= 1) {
+      __syncthreads();
+      if (tid < T) {
+        if (tid >= d) {
+          const int dd = dom[c][tid - d];
+          for (int ia = 0; ia < dd; ++ia) F[c ^ 1][ia][tid] = F[c][F[c][ia][tid - d]][tid];
+          dom[c ^ 1][tid] = (uint8_t)dd;
+        } else {
+          const int dd = dom[c][tid];
+          for (int ia = 0; ia < dd; ++ia) F[c ^ 1][ia][tid] = F[c][ia][tid];
+          dom[c ^ 1][tid] = (uint8_t)dd;
+        }
+      }
+      c ^= 1;
+    }
+    __syncthreads();
+    v = (tid == 0 || tid >= T) ? 0 : F[c][0][tid - 1];
+  }
+  if (tid < T) {
+    PartIter it = it0;  // as after phase 1's set-up: L = start of bucket j0
+    int64_t lprev = l0;
+    for (int64_t j = j0; j < j1; ++j) {
+      v = tab[lprev + v + (((lprev + v) >> 5) * padw)];
+      sp.out[j + 1] = it.L + v;  // position in bucket j
+      lprev = it.L;
+      it.next();
+    }
+  }
+  if (sp.sel) {  // positions -> original indices, four independent gathers per round
+    __syncthreads();
+    for (int64_t i = 1 + tid; i <= K; i += 4 * NT) {
+      int64_t q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = i + u * NT <= K ? sp.out[i + u * NT] : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = sp.sel[q[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u * NT <= K) sp.out[i + u * NT] = q[u];
+    }
+  }
+  if (tid == 0) {
+    sp.out[0] = index_of(sp, 0);
+    sp.out[K + 1] = index_of(sp, m - 1);
+    if (sp.out_count) *sp.out_count = sp.n_out;
+  }
+}
+
+}  // namespace
+}  // namespace mmlttb

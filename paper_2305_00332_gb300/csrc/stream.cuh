@@ -1,0 +1,388 @@
+// Device code of the MinMax preselection pass (Sec. 3 first step; MinMax of
+// Sec. 2.2.1, Table 1), shared by the split kernels (k_edges, k_stream) and the
+// fused single-cluster kernel.
+//
+// The interior points of every series are laid end to end in one global work space
+// (series_work in common.cuh), cut into W equal ranges, one per warp.  A warp walks
+// the bins that meet its range; for each piece it streams y with 16-byte coalesced
+// loads and keeps a per-lane first-occurrence argmin/argmax, then reduces across its
+// lane group and writes one Record at slot (global bin + warp).  x is never streamed:
+// bin bounds come from integer arithmetic (index bins) or from the bin-edge search.
+#pragma once
+
+#include "common.cuh"
+
+namespace mmlttb {
+namespace {
+
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream4u(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// NaN-propagating float min/max (a NaN operand makes the result NaN).
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// The high 32 bits of a double read as a float.  For doubles below 2^1017 in
+// magnitude this is a non-decreasing function of the double's value (the bit
+// patterns of both formats order like sign-magnitude integers), so
+// proxy(e) > proxy(m) implies e > m.  Larger magnitudes, inf and NaN map to NaN or
+// inf proxies, which the callers treat as "compare exactly".
+__device__ __forceinline__ float proxy_of_hi(unsigned hi) { return __uint_as_float(hi); }
+
+// Bin bounds of series sp (R2 index bins; R3 x-width bins via the edge array).
+// Bins cover the points [p0, p0 + nb): the interior for MinMax, all points for M4.
+__device__ __forceinline__ int64_t bin_start(const Batch& bt, const SeriesPlan& sp, int64_t b) {
+  if (sp.binmode == MMLTTB_BINS_INDEX) return sp.p0 + muldiv(b, sp.nb, sp.dB);
+  return bt.edges[sp.edge_off + b];
+}
+// The bin holding binned point p; warp-collective (every lane passes the same p).
+// x-width bins: a 32-ary search of the bin starts (three rounds for 8000 bins where
+// a binary search takes thirteen dependent loads).
+__device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesPlan& sp, int64_t p,
+                                                  int lane) {
+  if (sp.binmode == MMLTTB_BINS_INDEX) return part_of(p - sp.p0 + 1, sp.dnb, sp.B);
+  const int64_t* E = bt.edges + sp.edge_off;
+  int64_t lo = 0, hi = sp.B;  // the largest i < B with E[i] <= p lies in [lo, hi); E[0] <= p
+  while (hi - lo > 1) {
+    const int64_t step = (hi - lo + 31) >> 5;
+    const int64_t q = lo + (int64_t)lane * step;
+    const unsigned le = __ballot_sync(kFull, q < hi && E[q] <= p);  // a prefix of the lanes
+    const int64_t last = lo + (int64_t)(31 - __clz(le)) * step;
+    hi = last + step < hi ? last + step : hi;
+    lo = last;
+  }
+  return lo;
+}
+
+// First-occurrence argmin/argmax of y[lo, hi) for float32 y by one group of G lanes
+// (gl = lane within the group, gmask = the group's lanes; G = 32: the whole warp).
+// kNanAware: NaN-aware mode (R18): a bin holding a NaN reports its first NaN as both
+// extremes; its record carries the keys LLONG_MIN / LLONG_MAX, which no value has,
+// so merging records keeps the first NaN of the bin.
+template <int kUnroll, bool kNanAware>
+__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  const float inf = __int_as_float(0x7f800000);
+  // Empty state: only strictly smaller (larger) values are recorded, so a lane that
+  // sees nothing but +inf (-inf) keeps offset ~0u; if every lane does, the extreme is
+  // the first point (offset 0).
+  float mn = inf, mx = -inf;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
+  const uintptr_t ybase = (uintptr_t)y;
+  const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
+  const uintptr_t aend = ybase + (uintptr_t)hi * 4u;
+  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
+  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 4 - lo);  // in [-3, 0]
+  const float4* vp = (const float4*)a0;
+  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
+    float4 buf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + G * u;
+      if (vi < nvec) buf[u] = ld_stream4(vp + vi);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + G * u;
+      if (vi < nvec) {
+        const int32_t r = rel0 + 4 * (int32_t)vi;
+        const float e[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
+        float fm[4], fx[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const bool ok = (uint32_t)(r + k) < len;
+          fm[k] = ok ? e[k] : inf;
+          fx[k] = ok ? e[k] : -inf;
+        }
+        if (kNanAware && onan == 0xffffffffu) {
+          const bool any = (e[0] != e[0]) | (e[1] != e[1]) | (e[2] != e[2]) | (e[3] != e[3]);
+          if (any) {
+#pragma unroll
+            for (int k = 3; k >= 0; k--)  // lowest valid NaN of the vector
+              if ((uint32_t)(r + k) < len && e[k] != e[k]) onan = (uint32_t)(r + k);
+          }
+        }
+        const float m4 = fminf(fminf(fm[0], fm[1]), fminf(fm[2], fm[3]));
+        const float x4 = fmaxf(fmaxf(fx[0], fx[1]), fmaxf(fx[2], fx[3]));
+        if (m4 < mn) {  // rare: some element is a new strict minimum
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (fm[k] < mn) { mn = fm[k]; omn = (uint32_t)(r + k); }
+        }
+        if (x4 > mx) {
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (fx[k] > mx) { mx = fx[k]; omx = (uint32_t)(r + k); }
+        }
+      }
+    }
+  }
+  const int kmn = key32(mn), kmx = key32(mx);
+  const int wmn = __reduce_min_sync(gmask, kmn);
+  const unsigned wo = __reduce_min_sync(gmask, kmn == wmn ? omn : 0xffffffffu);
+  const int wmx = __reduce_max_sync(gmask, kmx);
+  const unsigned wx = __reduce_min_sync(gmask, kmx == wmx ? omx : 0xffffffffu);
+  Record r;
+  r.kmin = wmn;
+  r.kmax = wmx;
+  r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
+  r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
+  if (kNanAware) {
+    const unsigned wn = __reduce_min_sync(gmask, onan);
+    if (wn != 0xffffffffu) {
+      r.kmin = LLONG_MIN;
+      r.kmax = LLONG_MAX;
+      r.imin = r.imax = lo + (int64_t)wn;
+    }
+  }
+  return r;
+}
+
+// Warp-wide first-occurrence argmin/argmax of y[lo, hi) for float64 y.  The hot
+// loop issues no FP64 instruction (FP64 is a narrow pipe on this part): a float
+// compare of the high-word proxies rules out almost every element, and the rest
+// are compared exactly through order-preserving int64 keys.
+template <int kUnroll, bool kNanAware>
+__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  // Empty state: keys beyond every double's key and NaN proxies, so the first
+  // element a lane sees takes the exact path and is recorded.
+  long long kmn = LLONG_MAX, kmx = LLONG_MIN;
+  float pmn = __int_as_float(0x7fc00000), pmx = pmn;
+  uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
+  const uintptr_t ybase = (uintptr_t)y;
+  const uintptr_t a0 = (ybase + (uintptr_t)lo * 8u) & ~(uintptr_t)15;
+  const uintptr_t aend = ybase + (uintptr_t)hi * 8u;
+  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
+  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 8 - lo);  // in [-1, 0]
+  const float inf = __int_as_float(0x7f800000);
+  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
+    uint4 buf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + G * u;
+      if (vi < nvec) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u));
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      int64_t vi = v + G * u;
+      if (vi < nvec) {
+        const int32_t r = rel0 + 2 * (int32_t)vi;
+        const bool ok0 = (uint32_t)r < len, ok1 = (uint32_t)(r + 1) < len;
+        const float p0 = proxy_of_hi(buf[u].y), p1 = proxy_of_hi(buf[u].w);
+        const float pm = fmin_nan(ok0 ? p0 : inf, ok1 ? p1 : inf);
+        const float px = fmax_nan(ok0 ? p0 : -inf, ok1 ? p1 : -inf);
+        const bool need_min = !(pm > pmn);
+        const bool need_max = !(px < pmx);
+        if (need_min || need_max) {  // rare: exact comparison through int64 keys
+          const long long e0 = ((long long)buf[u].y << 32) | buf[u].x;
+          const long long e1 = ((long long)buf[u].w << 32) | buf[u].z;
+          const long long k0 = key64(__longlong_as_double(e0));
+          const long long k1 = key64(__longlong_as_double(e1));
+          if (kNanAware && onan == 0xffffffffu) {  // NaN proxies always take this path
+            const long long m = 0x7fffffffffffffffLL, inf_bits = 0x7ff0000000000000LL;
+            if (ok1 && (e1 & m) > inf_bits) onan = (uint32_t)(r + 1);
+            if (ok0 && (e0 & m) > inf_bits) onan = (uint32_t)r;
+          }
+          if (ok0 && k0 < kmn) { kmn = k0; omn = (uint32_t)r; pmn = p0; }
+          if (ok1 && k1 < kmn) { kmn = k1; omn = (uint32_t)(r + 1); pmn = p1; }
+          if (ok0 && k0 > kmx) { kmx = k0; omx = (uint32_t)r; pmx = p0; }
+          if (ok1 && k1 > kmx) { kmx = k1; omx = (uint32_t)(r + 1); pmx = p1; }
+        }
+      }
+    }
+  }
+  // int64 order = (signed high word, unsigned low word)
+  const int hmn = (int)(kmn >> 32);
+  const unsigned lmn = (unsigned)kmn;
+  const int whm = __reduce_min_sync(gmask, hmn);
+  const unsigned wlm = __reduce_min_sync(gmask, hmn == whm ? lmn : 0xffffffffu);
+  const bool eqm = (hmn == whm) && (lmn == wlm);
+  const unsigned wo = __reduce_min_sync(gmask, eqm ? omn : 0xffffffffu);
+  const int hmx = (int)(kmx >> 32);
+  const unsigned lmx = (unsigned)kmx;
+  const int whx = __reduce_max_sync(gmask, hmx);
+  const unsigned wlx = __reduce_max_sync(gmask, hmx == whx ? lmx : 0u);
+  const bool eqx = (hmx == whx) && (lmx == wlx);
+  const unsigned wx = __reduce_min_sync(gmask, eqx ? omx : 0xffffffffu);
+  Record r;
+  r.kmin = ((long long)whm << 32) | wlm;
+  r.kmax = ((long long)whx << 32) | wlx;
+  r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
+  r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
+  if (kNanAware) {
+    const unsigned wn = __reduce_min_sync(gmask, onan);
+    if (wn != 0xffffffffu) {
+      r.kmin = LLONG_MIN;
+      r.kmax = LLONG_MAX;
+      r.imin = r.imax = lo + (int64_t)wn;
+    }
+  }
+  return r;
+}
+
+// Smallest interior point q in [0, N] whose work unit floor(q*D/N) is >= t, for
+// 0 <= t <= D: ceil(t*N/D).
+__device__ __forceinline__ int64_t point_at_work(int64_t t, int64_t N, const Div& D) {
+  return muldiv_ceil(t, N, D);
+}
+
+// One warp over the binned points [p_lo, p_hi) of one series.  The warp splits into
+// 32/G groups of G lanes (G chosen per series from its mean bin size) and each group
+// works on its own bin, so small bins are processed 32/G at a time.
+template <int kUnroll>
+__device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t p_lo,
+                                  int64_t p_hi, int64_t w, int lane) {
+  const int G = sp.group;
+  const int ngroups = 32 / G;
+  const int grp = lane / G, gl = lane - grp * G;
+  const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
+  const bool ib = sp.binmode == MMLTTB_BINS_INDEX;
+  int64_t b = bin_containing(bt, sp, p_lo, lane);
+  // index bins: L = floor(mb*nb/B) and rem = mb*nb - L*B for this group's bin mb,
+  // stepped by 32/G bins per round with the plan's constants (no division per bin)
+  int64_t L = 0;
+  int32_t rem = 0;
+  if (ib) {
+    const int64_t mb0 = b + grp;
+    L = muldiv(mb0, sp.nb, sp.dB);
+    rem = (int32_t)((uint64_t)mb0 * (uint64_t)sp.nb - (uint64_t)L * (uint64_t)sp.B);
+  }
+  for (;;) {
+    const int64_t mb = b + grp;
+    int64_t lo = p_hi, hi = p_hi, sb1 = sp.p0 + sp.nb;
+    if (mb < sp.B) {
+      int64_t sb;
+      if (ib) {
+        sb = sp.p0 + L;
+        if (mb + 1 < sp.B) sb1 = sb + sp.bin_q1 + (rem + sp.bin_r1 >= sp.B ? 1 : 0);
+      } else {
+        sb = bin_start(bt, sp, mb);
+        if (mb + 1 < sp.B) sb1 = bin_start(bt, sp, mb + 1);
+      }
+      lo = sb > p_lo ? sb : p_lo;
+      hi = sb1 < p_hi ? sb1 : p_hi;
+    }
+    if (lo < hi) {
+      Record r;
+      if (sp.nan_aware)
+        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G, gmask)
+                                   : segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G, gmask);
+      else
+        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G, gmask)
+                                   : segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G, gmask);
+      if (gl == 0) bt.rec[sp.bin_off + mb + w] = r;
+    }
+    // the round ends with bin b + ngroups - 1 (held by the last group)
+    const int64_t last_end = __shfl_sync(kFull, sb1, 31);
+    if (last_end >= p_hi || b + ngroups >= sp.B) break;
+    b += ngroups;
+    if (ib) {
+      L += sp.bin_qs;
+      rem += sp.bin_rs;
+      if (rem >= sp.B) {
+        rem -= (int32_t)sp.B;
+        L += 1;
+      }
+    }
+  }
+}
+
+
+// Streaming warp w of the launch: every bin piece of every series in its range.
+template <int U>
+__device__ void stream_warp(const Batch& bt, int64_t w, int lane) {
+  int64_t g = warp_begin(w, bt.total_pos, bt.dwarps);
+  const int64_t g_end = warp_begin(w + 1, bt.total_pos, bt.dwarps);
+  int s = bt.pos_offs ? upper_index(bt.pos_offs, bt.n_series, g) : 0;
+  while (g < g_end && s < bt.n_series) {
+    const SeriesPlan& sp = plan_of(bt, s);
+    const int64_t send = sp.pos_off + sp.npos;
+    const int64_t seg_end = send < g_end ? send : g_end;
+    if (seg_end > g) {
+      // binned points whose work unit lies in [g, seg_end): p0 + q, q in [q_lo, q_hi)
+      const int64_t q_lo = point_at_work(g - sp.pos_off, sp.nb, sp.dnpos);
+      const int64_t q_hi = point_at_work(seg_end - sp.pos_off, sp.nb, sp.dnpos);
+      if (q_hi > q_lo) warp_series_range<U>(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
+      g = seg_end;
+    }
+    ++s;
+  }
+}
+
+// Bin edge e of the launch (all 32 lanes of a warp call it with the same e):
+// S_b = first binned point with x >= e_b, e_b = x_0 + floor(b (x_{n-1} - x_0) / B)
+// (R3, R16; FP64 edges on float64 x, R17); S_0 = p0, S_B = p0 + nb.  A 32-ary search:
+// each round the lanes probe 32 equally spaced points and keep the interval that
+// holds the first probe at or after the edge.
+__device__ int64_t edge_at(const Batch& bt, int64_t e, int lane) {
+  const int s = bt.edge_offs ? upper_index(bt.edge_offs, bt.n_series, e) : 0;
+  const SeriesPlan& sp = plan_of(bt, s);
+  const int64_t b = e - sp.edge_off;
+  int64_t res;
+  if (sp.nb < 1 || b == 0) {
+    res = sp.p0;
+  } else if (b >= sp.B) {
+    res = sp.p0 + sp.nb;
+  } else {
+    // left edge e_b: int64 x exact (R3); float64 x with every operation rounded (R17)
+    const bool fx = sp.xk == MMLTTB_X_F64;
+    const long long* x = (const long long*)sp.x;
+    const double* xd = (const double*)sp.x;
+    long long eb = 0;
+    double ebf = 0.0;
+    if (fx) {
+      const double x0 = __ldg(xd), D = __dsub_rn(__ldg(xd + sp.n - 1), x0);
+      ebf = __dadd_rn(x0, __ddiv_rn(__dmul_rn((double)b, D), (double)sp.B));
+    } else {
+      const long long x0 = __ldg(x), xl = __ldg(x + sp.n - 1);
+      eb = x0 + (long long)muldiv(b, xl - x0, sp.dB);
+    }
+    auto at_or_after = [&](int64_t q) { return fx ? __ldg(xd + q) >= ebf : __ldg(x + q) >= eb; };
+    int64_t lo = sp.p0, hi = sp.p0 + sp.nb;  // answer in [lo, hi]
+    while (hi - lo > 32) {
+      const int64_t step = (hi - lo + 31) / 32;
+      const int64_t q = lo + (int64_t)lane * step;
+      const bool pred = q < hi && at_or_after(q);
+      const unsigned m = __ballot_sync(kFull, pred);
+      if (m == 0) {
+        const int64_t last = lo + ((hi - lo - 1) / step) * step;  // last sampled point
+        lo = last + 1;
+      } else {
+        const int f = __ffs(m) - 1;
+        const int64_t qf = lo + (int64_t)f * step;
+        lo = f > 0 ? qf - step + 1 : lo;
+        hi = qf;
+      }
+    }
+    const int64_t q = lo + lane;
+    const bool pred = q < hi && at_or_after(q);
+    const unsigned m = __ballot_sync(kFull, pred);
+    res = m ? lo + (__ffs(m) - 1) : hi;
+  }
+  return res;
+}
+
+}  // namespace
+}  // namespace mmlttb

@@ -69,3 +69,12 @@ def _call_minmaxlttb(lib, y, ydt, x, xk, n, n_out, r_ps, binmode, out, cap):
 ])
 def test_host_side_validation(lib, args, code):
     assert _call_minmaxlttb(lib, *args) == code
+
+
+def test_single_path_preference_is_validated_on_the_host(lib):
+    f = lib.mmlttb_set_single_path
+    f.argtypes = [ctypes.c_int]
+    for bad in (-1, 4, 99):
+        assert f(bad) == -1
+    for good in (1, 2, 3, 0):  # ends on AUTO
+        assert f(good) == 0
