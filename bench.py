@@ -362,21 +362,32 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+# Sources the streaming kernel is compiled from; the ncu summary records their hash.
+STREAM_SOURCES = ("minmax.cu", "stream.cuh", "common.cuh")
+
+
+def stream_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STREAM_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2305_00332_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "mmlttb.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(n):
     """DRAM bytes per launch of the streaming kernel from the committed ncu summary,
-    scaled to n points; None when the summary is absent or the kernel source changed."""
-    import hashlib
+    scaled to n points; None when the summary is absent or the kernel's sources
+    changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "k_stream_xwidth_f64.md")
-    src = os.path.join(ROOT, "paper_2305_00332_gb300", "csrc", "minmax.cu")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     kv = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("minmax.cu sha256[:16]") != h:
+    if kv.get("kernel sources sha256[:16]") != stream_source_hash():
         return None
     try:
         per_point = float(kv["dram bytes per point"])

@@ -186,6 +186,8 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     off = align256(off + (size_t)p.nct * 4);
     p.off_ctaoff = off;
     off = align256(off + (size_t)p.nct * 8);
+  }
+  if (p.branch != BR_ARANGE) {  // per-CTA words of the fused kernel
     p.off_ftot = off;
     off = align256(off + (size_t)d.sms * 8);
   }
@@ -328,6 +330,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   if (path != MMLTTB_PATH_SPLIT) {
     const int G = d.fused_grid;
     bt.chain_smem = fused_tab_smem(p.tab_cap);
+    bt.dgrid = make_div(G);
     // the header words (status, barrier) are cleared by the first kernel of the
     // call, or by a memset when the fused kernel is the first
     const bool lead = path == MMLTTB_PATH_FUSED_TAIL && (bt.total_edges > 0 || p.W > 0);

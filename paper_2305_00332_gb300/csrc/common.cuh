@@ -124,6 +124,7 @@ struct Batch {
   int64_t total_pos;   // sum of npos: the total work the streaming warps split evenly
   int64_t n_warps;     // streaming warps, each with at least one interior point
   Div dtotal, dwarps;  // divisors total_pos and n_warps (set_warp_divs)
+  Div dgrid;           // divisor gridDim.x of the fused kernel
   int64_t total_edges; // sum over x-width series of B+1
   int64_t total_slots; // sum of tab_cap
   int64_t total_bin_ctas;  // compaction CTAs over all minmax series

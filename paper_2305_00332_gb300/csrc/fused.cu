@@ -11,9 +11,11 @@
 //   compaction  pass 1: CTA c resolves its contiguous share of the bins and
 //               publishes how many indices they emit; pass 2: every CTA sums the
 //               totals before it and places its bins' indices
-//   tables      one transition-table entry per position, bucket-major, over every
-//               SM (the FP64 areas are the costly part, and the FP64 pipe is narrow)
-//   chain       CTA 0 resolves the LTTB chain and writes the output
+//   LTTB        buckets of at most 8 positions: every CTA forms the picks of its
+//               buckets, composes them and, after one barrier, resolves its share
+//               of the chain (lttb_by_ctas).  Larger buckets: the transition tables
+//               over every SM, a barrier, then CTA 0 resolves the chain.  (The FP64
+//               areas are the costly part, and the FP64 pipe is narrow.)
 //
 // With kStream = false the kernel is the tail of a large series: k_edges and
 // k_stream run before it, and it starts on their records.
@@ -77,10 +79,136 @@ __device__ __forceinline__ long long warp_sum64(long long v) {
   return v;
 }
 
+// LTTB on the preselected positions of a single series whose buckets hold at most 8
+// positions (MinMaxLTTB with r_ps up to 7), on every CTA of the grid at once.  CTA c
+// owns buckets [jc0, jc1):
+//   1. the picks after every position of the bucket before (bucket_pick), packed
+//      into one map of 8 bytes per bucket (entry offset -> pick offset);
+//   2. an inclusive block scan of the bucket maps under composition, so each bucket
+//      holds the map from the pick before jc0 to its own pick;
+//   3. the CTA publishes its total map; after a grid barrier every CTA composes the
+//      maps of the CTAs before it (a warp reduction in CTA order) and evaluates the
+//      result at the chain's start, position 0: the pick before jc0;
+//   4. every bucket's pick is one byte lookup; the picks become indices.
+// The sequential chain of Sec. 2.2.1 is resolved exactly: every map entry is a pick
+// the sequential method would make from that previous pick.  s_lo/s_hi hold 4096
+// maps each.  Returns false when the barrier timed out.
+__device__ bool lttb_by_ctas(const Batch& bt, const SeriesPlan& sp, int64_t m, int lgS,
+                             unsigned* s_lo, unsigned* s_hi) {
+  __shared__ unsigned s_wl[kFusedWarps], s_wh[kFusedWarps];
+  __shared__ unsigned s_cl, s_ch;
+  __shared__ int s_entry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c = blockIdx.x;
+  const int64_t K = sp.n_out - 2, N = m - 2;
+  const int64_t jc0 = muldiv(c, K, bt.dgrid), jc1 = muldiv(c + 1, K, bt.dgrid);
+  const int64_t nbk = jc1 - jc0;
+  const int S = 1 << lgS;
+  // 1. bucket maps
+  for (int64_t base = (int64_t)warp * 32; base < (nbk << lgS); base += kFusedThreads) {
+    const int64_t slot = base + lane;
+    const int64_t jj = slot >> lgS;
+    const int k = (int)(slot & (S - 1));
+    int64_t p;
+    bool valid;
+    const int pick = bucket_pick(sp, m, jj < nbk ? jc0 + jj : K, k, lgS, lane, &p, &valid);
+    unsigned wl = 0u, wh = 0u;
+    if (valid) {
+      if (k < 4) wl = (unsigned)pick << (8 * k);
+      else wh = (unsigned)pick << (8 * (k - 4));
+    }
+    for (int d = 1; d < S; d <<= 1) {
+      wl |= __shfl_xor_sync(kFull, wl, d);
+      wh |= __shfl_xor_sync(kFull, wh, d);
+    }
+    if (k == 0 && jj < nbk) {
+      s_lo[jj] = wl;
+      s_hi[jj] = wh;
+    }
+  }
+  __syncthreads();
+  // 2. prefix of the bucket maps within the CTA
+  Map8 carry = kIdentity8;
+  for (int64_t t0 = 0; t0 < nbk; t0 += kFusedThreads) {
+    const int64_t i = t0 + tid;
+    Map8 P = i < nbk ? Map8{s_lo[i], s_hi[i]} : kIdentity8;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const Map8 o = shfl_up_map(P, d);
+      if (lane >= d) P = compose(P, o);
+    }
+    if (lane == 31) {
+      s_wl[warp] = P.lo;
+      s_wh[warp] = P.hi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      Map8 W = lane < kFusedWarps ? Map8{s_wl[lane], s_wh[lane]} : kIdentity8;
+#pragma unroll
+      for (int d = 1; d < kFusedWarps; d <<= 1) {
+        const Map8 o = shfl_up_map(W, d);
+        if (lane >= d) W = compose(W, o);
+      }
+      Map8 E = shfl_up_map(W, 1);
+      if (lane == 0) E = kIdentity8;
+      E = compose(E, carry);  // everything before this warp, earlier tiles first
+      const Map8 total = compose(shfl_map(W, kFusedWarps - 1), carry);
+      if (lane < kFusedWarps) {
+        s_wl[lane] = E.lo;
+        s_wh[lane] = E.hi;
+      }
+      if (lane == 0) {
+        s_cl = total.lo;
+        s_ch = total.hi;
+      }
+    }
+    __syncthreads();
+    P = compose(P, Map8{s_wl[warp], s_wh[warp]});
+    if (i < nbk) {
+      s_lo[i] = P.lo;
+      s_hi[i] = P.hi;
+    }
+    carry = Map8{s_cl, s_ch};
+    __syncthreads();
+  }
+  // 3. the CTA's map for the others, then the pick before this CTA's first bucket
+  if (tid == 0) bt.fused_tot[c] = (long long)(((unsigned long long)carry.hi << 32) | carry.lo);
+  if (!grid_sync(bt)) return false;
+  if (warp == 0) {
+    const int64_t q = (c + 31) >> 5;  // CTAs per lane, in order
+    Map8 A = kIdentity8;
+    for (int64_t k2 = (int64_t)lane * q; k2 < (int64_t)(lane + 1) * q && k2 < c; ++k2) {
+      const unsigned long long v = (unsigned long long)bt.fused_tot[k2];
+      A = compose(Map8{(unsigned)v, (unsigned)(v >> 32)}, A);
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {  // lane i (earlier CTAs) then lane i + d
+      const Map8 o = shfl_down_map(A, d);
+      if ((lane & (2 * d - 1)) == 0) A = compose(o, A);
+    }
+    if (lane == 0) s_entry = map_at(A, 0);  // the chain starts at position 0
+  }
+  __syncthreads();
+  const int e = s_entry;
+  // 4. picks -> output indices
+  for (int64_t jj = tid; jj < nbk; jj += kFusedThreads) {
+    const int64_t j = jc0 + jj;
+    const int off = map_at(Map8{s_lo[jj], s_hi[jj]}, e);
+    sp.out[j + 1] = index_of(sp, part_start(j, N, sp.dK) + off);
+  }
+  if (c == 0 && tid == 0) {
+    sp.out[0] = index_of(sp, 0);
+    sp.out[K + 1] = index_of(sp, m - 1);
+    if (sp.out_count) *sp.out_count = sp.n_out;
+  }
+  return true;
+}
+
 template <bool kStream>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constant__ Batch bt) {
-  // chain scratch (CTA 0): F[c][ia][t] = thread t's map, entry ia
-  __shared__ uint8_t F[2][kTableMaxBucket][kFusedThreads];
+  // chain scratch: F[c][ia][t] = thread t's map, entry ia (CTA 0), or the bucket maps
+  // of lttb_by_ctas (every CTA)
+  __shared__ __align__(16) uint8_t F[2][kTableMaxBucket][kFusedThreads];
   __shared__ uint8_t dom[2][kFusedThreads];
   __shared__ long long s_warp[kFusedWarps];
   __shared__ long long s_base, s_grand;
@@ -167,6 +295,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
   if (sp.engine != EN_TABLES) return;
   {
     const int64_t m = lttb_m(sp);
+    if (m > sp.n_out) {
+      const int64_t K = sp.n_out - 2;
+      const int64_t bmax = (int64_t)div_by((uint64_t)(m - 2 + K - 1), sp.dK);  // largest bucket
+      int lgS = 0;
+      while ((int64_t(1) << lgS) < bmax) ++lgS;
+      const int64_t per_cta = (int64_t)div_by((uint64_t)(K + G - 1), bt.dgrid);
+      if (lgS <= 3 && per_cta <= 4096) {
+        lttb_by_ctas(bt, sp, m, lgS, (unsigned*)&F[0][0][0], (unsigned*)&F[0][0][0] + 4096);
+        return;
+      }
+    }
     const int64_t nslots = m > sp.n_out ? (sp.n_out - 2) << sp.tab_lgS : 0;
     // warp-sized slot blocks dealt round-robin over the CTAs, so the FP64 area work
     // of a small table spreads over every SM

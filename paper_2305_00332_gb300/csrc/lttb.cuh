@@ -155,21 +155,24 @@ __device__ void table_entry(const Batch& bt, int64_t slot, int lane) {
   sp.tab[p] = (uint8_t)pick;
 }
 
-// Table entries of one series laid out bucket-major: slot j*S + k (S = 2^tab_lgS,
-// at least the largest bucket) is the entry of the k-th position of bucket j-1 (of
-// position 0 for j = 0), which picks in bucket j.  Warp-collective (all 32 lanes,
-// S lanes per bucket).  The bucket follows from the slot by a shift and the bucket
-// starts step from one floor(j*N/K), so nothing divides by the position count; the
-// first lane of a bucket forms the mean of bucket j+1 (R7) for all S lanes.
-__device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot, int lane) {
-  const int lgS = sp.tab_lgS, S = 1 << lgS;
+// The LTTB pick that follows the k-th position of bucket j-1 (position 0 for j = 0):
+// the offset in bucket j of the point with the largest area against that position
+// and the mean of bucket j+1 (R1, R5-R8).  Warp-collective: all 32 lanes call it,
+// the 2^lgS lanes of a bucket (lane groups aligned to 2^lgS) with the same j; the
+// first lane of a bucket forms the mean (R7) for all of them.  The bucket starts
+// step from one floor(j*N/K), so nothing divides by the position count.  *pos
+// receives the position whose entry this is; the result is meaningful only where
+// *valid (j < K and k inside bucket j-1).
+__device__ int bucket_pick(const SeriesPlan& sp, int64_t m, int64_t j, int k, int lgS, int lane,
+                           int64_t* pos, bool* valid) {
+  const int S = 1 << lgS;
   const int64_t K = sp.n_out - 2, N = m - 2;
-  const int64_t j = slot >> lgS;
-  const int k = (int)(slot & (S - 1));
   bool work = false;
   int64_t p = 0, lo = 0, hi = 0;
   double xc = 0.0, yc = 0.0, xa = 0.0, ya = 0.0;
-  double xb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
+  double xb[8], yb[8];  // candidates; buckets of up to 8 load before the mean is formed
+#pragma unroll
+  for (int u = 0; u < 8; ++u) xb[u] = yb[u] = 0.0;
   if (j < K) {
     StepDiv bs;
     int64_t lprev = 0;
@@ -188,7 +191,7 @@ __device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot
     if (work) {
       pos_xy(sp, p, &xa, &ya);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)  // the first candidates load while the mean is formed
+      for (int u = 0; u < 8; ++u)
         if (lo + u < hi) pos_xy(sp, lo + u, &xb[u], &yb[u]);
     }
     if (k == 0) {
@@ -204,17 +207,19 @@ __device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot
   const int leader = lane & ~(S - 1);
   xc = __shfl_sync(kFull, xc, leader);
   yc = __shfl_sync(kFull, yc, leader);
-  if (!work) return;
+  *pos = p;
+  *valid = work;
+  if (!work) return 0;
   long long best = -1;  // bits of a non-negative double order like the double
   int pick = 0;
-  for (int64_t q0 = lo; q0 < hi; q0 += 4) {
+  for (int64_t q0 = lo; q0 < hi; q0 += 8) {
     if (q0 > lo) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 8; ++u)
         if (q0 + u < hi) pos_xy(sp, q0 + u, &xb[u], &yb[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       if (q0 + u >= hi) break;
       const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], xc, yc));
       if (q0 + u == lo || ab > best) {  // R8: the first largest wins
@@ -223,7 +228,17 @@ __device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot
       }
     }
   }
-  sp.tab[p] = (uint8_t)pick;
+  return pick;
+}
+
+// Table entries of one series laid out bucket-major: slot j*S + k (S = 2^tab_lgS,
+// at least the largest bucket) holds the pick after the k-th position of bucket j-1.
+__device__ void table_bucket_entry(const SeriesPlan& sp, int64_t m, int64_t slot, int lane) {
+  const int lgS = sp.tab_lgS;
+  int64_t p;
+  bool valid;
+  const int pick = bucket_pick(sp, m, slot >> lgS, (int)(slot & ((1 << lgS) - 1)), lgS, lane, &p, &valid);
+  if (valid) sp.tab[p] = (uint8_t)pick;
 }
 
 // Bucket starts L_j = floor(j*N/K)+1 for consecutive j without a division per step.
@@ -260,6 +275,13 @@ __device__ __forceinline__ int map_at(Map8 a, int i) {
 __device__ __forceinline__ Map8 shfl_up_map(Map8 a, int d) {
   return {__shfl_up_sync(kFull, a.lo, d), __shfl_up_sync(kFull, a.hi, d)};
 }
+__device__ __forceinline__ Map8 shfl_down_map(Map8 a, int d) {
+  return {__shfl_down_sync(kFull, a.lo, d), __shfl_down_sync(kFull, a.hi, d)};
+}
+__device__ __forceinline__ Map8 shfl_map(Map8 a, int src) {
+  return {__shfl_sync(kFull, a.lo, src), __shfl_sync(kFull, a.hi, src)};
+}
+constexpr Map8 kIdentity8 = {0x03020100u, 0x07060504u};
 
 // The LTTB output of series sp once its tables are written.  Block-collective over
 // NT threads.  F ([2][kTableMaxBucket][NT]) and dom ([2][NT]) are shared scratch;
