@@ -102,8 +102,9 @@ __global__ void __launch_bounds__(kGridThreads) k_lttb_grid(const __grid_constan
   if (m <= sp.n_out) return;  // k_chain copied the points
   const int64_t K = sp.n_out - 2, N = m - 2;
   const int64_t G = gridDim.x, c = blockIdx.x;
-  // Phase A: every next-bucket mean, one thread per bucket.
-  for (int64_t j = c * blockDim.x + threadIdx.x; j < K; j += G * blockDim.x) {
+  // Phase A: every next-bucket mean, one thread per bucket, dealt round-robin over the
+  // CTAs: each mean is a long dependent FP64 sum, and the FP64 pipe is narrow.
+  for (int64_t j = (int64_t)threadIdx.x * G + c; j < K; j += G * blockDim.x) {
     int64_t lo, hi;
     next_bucket(j, sp.dK, N, m, &lo, &hi);
     bucket_mean(sp, lo, hi, &sp.means[2 * j], &sp.means[2 * j + 1]);

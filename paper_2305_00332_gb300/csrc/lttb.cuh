@@ -32,30 +32,29 @@ __device__ void bucket_mean(const SeriesPlan& sp, int64_t lo, int64_t hi, double
     // integers below 2^53, so the sequential FP64 sum is exact and equals the
     // closed form.
     sx = (double)((lo + hi - 1) * (hi - lo) / 2);
-    for (int64_t p = lo; p < hi; p += 4) {
-      double yv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) yv[u] = p + u < hi ? y_of(sp, p + u) : 0.0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (p + u < hi) sy = __dadd_rn(sy, yv[u]);
+    for (int64_t p = lo; p < hi; ++p) sy = __dadd_rn(sy, y_of(sp, p));
+  } else if (hi - lo > 8) {
+    for (int64_t p = lo; p < hi; ++p) {
+      double xp, yp;
+      pos_xy(sp, p, &xp, &yp);
+      sx = __dadd_rn(sx, xp);
+      sy = __dadd_rn(sy, yp);
     }
   } else {
-    // four points' loads in flight, then the sums in order (left to right)
-    for (int64_t p = lo; p < hi; p += 4) {
-      double xv[4], yv[4];
+    // a small bucket (after preselection): its loads in flight together, then the
+    // sums in order (left to right)
+    double xv[8], yv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        xv[u] = yv[u] = 0.0;
-        if (p + u < hi) pos_xy(sp, p + u, &xv[u], &yv[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (p + u < hi) {
-          sx = __dadd_rn(sx, xv[u]);
-          sy = __dadd_rn(sy, yv[u]);
-        }
+    for (int u = 0; u < 8; ++u) {
+      xv[u] = yv[u] = 0.0;
+      if (lo + u < hi) pos_xy(sp, lo + u, &xv[u], &yv[u]);
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (lo + u < hi) {
+        sx = __dadd_rn(sx, xv[u]);
+        sy = __dadd_rn(sy, yv[u]);
+      }
   }
   const double cnt = (double)(hi - lo);
   *xc = __ddiv_rn(sx, cnt);
