@@ -357,7 +357,8 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
-      if ((e = launch_stream(bt, grid, p.variant, st)) != cudaSuccess) return cuda_fail(e);
+      if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+        return cuda_fail(e);
       stage_mark(st);
       ++g_launches;
       bt.zero_status = 0;
@@ -387,7 +388,8 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
-      if ((e = launch_stream(bt, grid, p.variant, st)) != cudaSuccess) return cuda_fail(e);
+      if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+        return cuda_fail(e);
       stage_mark(st);
       ++g_launches;
     }

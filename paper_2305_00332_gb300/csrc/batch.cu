@@ -104,6 +104,14 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
   for (int64_t s = 0; s < n; ++s)
     if (binned(b->plans[s].branch)) pts[b->plans[s].ydt == MMLTTB_F32 ? 0 : 1] += b->plans[s].nb;
   b->variant = stream_variant(d, pts[1] > pts[0] ? MMLTTB_F64 : MMLTTB_F32);
+  b->ymode = -1;  // the specialised stream kernel when every binned series shares one y mode
+  for (int64_t s = 0; s < n; ++s) {
+    const SeriesPlan& sp = b->plans[s];
+    if (!binned(sp.branch)) continue;
+    const int y = stream_ymode(sp.ydt, sp.nan_aware != 0);
+    b->ymode = (b->ymode < 0 || b->ymode == y) ? y : 0;
+  }
+  if (b->ymode < 0) b->ymode = 0;
   b->Wcap = stream_warp_cap(d);
   b->W = stream_warps(d, b->variant, pos);
   if (b->W > 0 && pos / b->W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;
@@ -213,7 +221,7 @@ int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
   }
   if (b->W > 0) {
     const int64_t grid = (b->W + kStreamWarps - 1) / kStreamWarps;
-    if ((e = launch_stream(bt, grid, b->variant, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_stream(bt, grid, b->variant, b->ymode, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
   if (b->total_bin_ctas > 0) {

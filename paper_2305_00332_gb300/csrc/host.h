@@ -50,6 +50,7 @@ struct BatchImpl {
   int64_t total_pos = 0, total_bins = 0, total_edges = 0, total_slots = 0;
   int64_t Wcap = 0, W = 0;
   int variant = 0;
+  int ymode = 0;  // stream-kernel y mode (stream_ymode) shared by every binned series, else 0
   bool any_block = false;
   int64_t max_tab = 0;  // largest per-series table storage (positions)
   int64_t total_bin_ctas = 0;

@@ -10,14 +10,14 @@ namespace mmlttb {
 
 namespace {
 
-template <int U, int MINB>
+template <int U, int MINB, int kY>
 __global__ void __launch_bounds__(kStreamThreads, MINB) k_stream(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
   if (bt.zero_status && blockIdx.x == 0 && threadIdx.x == 0) zero_header(bt);
   const int64_t w = (int64_t)blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
   if (w >= bt.n_warps) return;
-  stream_warp<U>(bt, w, threadIdx.x & 31);
+  stream_warp<U, kY>(bt, w, threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt) {
@@ -32,12 +32,21 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
 
 }  // namespace
 
-// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6).
-static const void* stream_kernel(int v) {
+// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6), each for any y, float32
+// and float64 y.
+template <int kY>
+static const void* stream_kernel_y(int v) {
   switch (v) {
-    case 1: return (const void*)k_stream<8, 3>;
-    case 2: return (const void*)k_stream<2, 6>;
-    default: return (const void*)k_stream<4, 4>;
+    case 1: return (const void*)k_stream<8, 3, kY>;
+    case 2: return (const void*)k_stream<2, 6, kY>;
+    default: return (const void*)k_stream<4, 4, kY>;
+  }
+}
+static const void* stream_kernel(int v, int ymode) {
+  switch (ymode) {
+    case kYF32: return stream_kernel_y<kYF32>(v);
+    case kYF64: return stream_kernel_y<kYF64>(v);
+    default: return stream_kernel_y<kYAny>(v);
   }
 }
 
@@ -51,10 +60,14 @@ int stream_variant_info(int v, int* unroll, int* min_blocks) {
 
 int stream_blocks_per_sm(int v) {
   int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v), kStreamThreads, 0) !=
-      cudaSuccess)
-    return 1;
-  return bps > 0 ? bps : 1;
+  int b0 = 0;
+  for (int y = kYAny; y <= kYF64; ++y) {  // the smallest occupancy of the variant's kernels
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v, y), kStreamThreads, 0) !=
+        cudaSuccess)
+      return 1;
+    if (y == kYAny || bps < b0) b0 = bps;
+  }
+  return b0 > 0 ? b0 : 1;
 }
 
 cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
@@ -64,13 +77,22 @@ cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
   return launch_pdl(k_edges, dim3((unsigned)grid), dim3(256), 0, st, bt);
 }
 
-cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, cudaStream_t st) {
+template <int kY>
+static cudaError_t launch_stream_y(const Batch& bt, dim3 g, dim3 b, int variant, cudaStream_t st) {
+  switch (variant) {
+    case 1: return launch_pdl(k_stream<8, 3, kY>, g, b, 0, st, bt);
+    case 2: return launch_pdl(k_stream<2, 6, kY>, g, b, 0, st, bt);
+    default: return launch_pdl(k_stream<4, 4, kY>, g, b, 0, st, bt);
+  }
+}
+
+cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode, cudaStream_t st) {
   if (bt.n_warps <= 0) return cudaSuccess;
   const dim3 g((unsigned)grid), b(kStreamThreads);
-  switch (variant) {
-    case 1: return launch_pdl(k_stream<8, 3>, g, b, 0, st, bt);
-    case 2: return launch_pdl(k_stream<2, 6>, g, b, 0, st, bt);
-    default: return launch_pdl(k_stream<4, 4>, g, b, 0, st, bt);
+  switch (ymode) {
+    case kYF32: return launch_stream_y<kYF32>(bt, g, b, variant, st);
+    case kYF64: return launch_stream_y<kYF64>(bt, g, b, variant, st);
+    default: return launch_stream_y<kYAny>(bt, g, b, variant, st);
   }
 }
 

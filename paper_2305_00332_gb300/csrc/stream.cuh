@@ -75,13 +75,88 @@ __device__ __forceinline__ int64_t bin_containing(const Batch& bt, const SeriesP
   return lo;
 }
 
+// (key, offset) reductions over the aligned group of G lanes holding this lane (G a
+// power of two), every lane of the warp taking part: the smallest key with its
+// smallest offset (argmin, first occurrence on ties) and the largest key with its
+// smallest offset.  A whole warp (G = 32) uses the warp reduction instructions;
+// smaller groups exchange with log2(G) xor shuffles, one instruction serving every
+// group of the warp (reductions over a sub-warp mask are issued once per group).
+__device__ __forceinline__ void group_arg32(int& kmn, unsigned& omn, int& kmx, unsigned& omx, int G) {
+  if (G == 32) {
+    const int wmn = __reduce_min_sync(kFull, kmn);
+    omn = __reduce_min_sync(kFull, kmn == wmn ? omn : 0xffffffffu);
+    kmn = wmn;
+    const int wmx = __reduce_max_sync(kFull, kmx);
+    omx = __reduce_min_sync(kFull, kmx == wmx ? omx : 0xffffffffu);
+    kmx = wmx;
+    return;
+  }
+  for (int d = 1; d < G; d <<= 1) {
+    const int a = __shfl_xor_sync(kFull, kmn, d);
+    const unsigned ao = __shfl_xor_sync(kFull, omn, d);
+    if (a < kmn || (a == kmn && ao < omn)) {
+      kmn = a;
+      omn = ao;
+    }
+    const int c = __shfl_xor_sync(kFull, kmx, d);
+    const unsigned co = __shfl_xor_sync(kFull, omx, d);
+    if (c > kmx || (c == kmx && co < omx)) {
+      kmx = c;
+      omx = co;
+    }
+  }
+}
+__device__ __forceinline__ void group_arg64(long long& kmn, unsigned& omn, long long& kmx, unsigned& omx,
+                                            int G) {
+  if (G == 32) {  // int64 order = (signed high word, unsigned low word)
+    const int hmn = (int)(kmn >> 32);
+    const unsigned lmn = (unsigned)kmn;
+    const int whm = __reduce_min_sync(kFull, hmn);
+    const unsigned wlm = __reduce_min_sync(kFull, hmn == whm ? lmn : 0xffffffffu);
+    const bool eqm = (hmn == whm) && (lmn == wlm);
+    omn = __reduce_min_sync(kFull, eqm ? omn : 0xffffffffu);
+    kmn = (long long)(((unsigned long long)(unsigned)whm << 32) | wlm);
+    const int hmx = (int)(kmx >> 32);
+    const unsigned lmx = (unsigned)kmx;
+    const int whx = __reduce_max_sync(kFull, hmx);
+    const unsigned wlx = __reduce_max_sync(kFull, hmx == whx ? lmx : 0u);
+    const bool eqx = (hmx == whx) && (lmx == wlx);
+    omx = __reduce_min_sync(kFull, eqx ? omx : 0xffffffffu);
+    kmx = (long long)(((unsigned long long)(unsigned)whx << 32) | wlx);
+    return;
+  }
+  for (int d = 1; d < G; d <<= 1) {
+    const long long a = __shfl_xor_sync(kFull, kmn, d);
+    const unsigned ao = __shfl_xor_sync(kFull, omn, d);
+    if (a < kmn || (a == kmn && ao < omn)) {
+      kmn = a;
+      omn = ao;
+    }
+    const long long c = __shfl_xor_sync(kFull, kmx, d);
+    const unsigned co = __shfl_xor_sync(kFull, omx, d);
+    if (c > kmx || (c == kmx && co < omx)) {
+      kmx = c;
+      omx = co;
+    }
+  }
+}
+__device__ __forceinline__ unsigned group_min_u32(unsigned v, int G) {
+  if (G == 32) return __reduce_min_sync(kFull, v);
+  for (int d = 1; d < G; d <<= 1) {
+    const unsigned o = __shfl_xor_sync(kFull, v, d);
+    v = o < v ? o : v;
+  }
+  return v;
+}
+
 // First-occurrence argmin/argmax of y[lo, hi) for float32 y by one group of G lanes
-// (gl = lane within the group, gmask = the group's lanes; G = 32: the whole warp).
+// (gl = lane within the group; G = 32: the whole warp).  Every lane of the warp calls
+// it (a group with nothing to do passes lo == hi).
 // kNanAware: NaN-aware mode (R18): a bin holding a NaN reports its first NaN as both
 // extremes; its record carries the keys LLONG_MIN / LLONG_MAX, which no value has,
 // so merging records keeps the first NaN of the bin.
 template <int kUnroll, bool kNanAware>
-__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
+__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G) {
   const uint32_t len = (uint32_t)(hi - lo);
   const float inf = __int_as_float(0x7f800000);
   // Empty state: only strictly smaller (larger) values are recorded, so a lane that
@@ -138,18 +213,16 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
       }
     }
   }
-  const int kmn = key32(mn), kmx = key32(mx);
-  const int wmn = __reduce_min_sync(gmask, kmn);
-  const unsigned wo = __reduce_min_sync(gmask, kmn == wmn ? omn : 0xffffffffu);
-  const int wmx = __reduce_max_sync(gmask, kmx);
-  const unsigned wx = __reduce_min_sync(gmask, kmx == wmx ? omx : 0xffffffffu);
+  int wmn = key32(mn), wmx = key32(mx);
+  unsigned wo = omn, wx = omx;
+  group_arg32(wmn, wo, wmx, wx, G);
   Record r;
   r.kmin = wmn;
   r.kmax = wmx;
   r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
   r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
   if (kNanAware) {
-    const unsigned wn = __reduce_min_sync(gmask, onan);
+    const unsigned wn = group_min_u32(onan, G);
     if (wn != 0xffffffffu) {
       r.kmin = LLONG_MIN;
       r.kmax = LLONG_MAX;
@@ -164,7 +237,7 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
 // compare of the high-word proxies rules out almost every element, and the rest
 // are compared exactly through order-preserving int64 keys.
 template <int kUnroll, bool kNanAware>
-__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G, unsigned gmask) {
+__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G) {
   const uint32_t len = (uint32_t)(hi - lo);
   // Empty state: keys beyond every double's key and NaN proxies, so the first
   // element a lane sees takes the exact path and is recorded.
@@ -213,26 +286,15 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, i
       }
     }
   }
-  // int64 order = (signed high word, unsigned low word)
-  const int hmn = (int)(kmn >> 32);
-  const unsigned lmn = (unsigned)kmn;
-  const int whm = __reduce_min_sync(gmask, hmn);
-  const unsigned wlm = __reduce_min_sync(gmask, hmn == whm ? lmn : 0xffffffffu);
-  const bool eqm = (hmn == whm) && (lmn == wlm);
-  const unsigned wo = __reduce_min_sync(gmask, eqm ? omn : 0xffffffffu);
-  const int hmx = (int)(kmx >> 32);
-  const unsigned lmx = (unsigned)kmx;
-  const int whx = __reduce_max_sync(gmask, hmx);
-  const unsigned wlx = __reduce_max_sync(gmask, hmx == whx ? lmx : 0u);
-  const bool eqx = (hmx == whx) && (lmx == wlx);
-  const unsigned wx = __reduce_min_sync(gmask, eqx ? omx : 0xffffffffu);
+  unsigned wo = omn, wx = omx;
+  group_arg64(kmn, wo, kmx, wx, G);
   Record r;
-  r.kmin = ((long long)whm << 32) | wlm;
-  r.kmax = ((long long)whx << 32) | wlx;
+  r.kmin = kmn;
+  r.kmax = kmx;
   r.imin = lo + (int64_t)(wo == 0xffffffffu ? 0u : wo);
   r.imax = lo + (int64_t)(wx == 0xffffffffu ? 0u : wx);
   if (kNanAware) {
-    const unsigned wn = __reduce_min_sync(gmask, onan);
+    const unsigned wn = group_min_u32(onan, G);
     if (wn != 0xffffffffu) {
       r.kmin = LLONG_MIN;
       r.kmax = LLONG_MAX;
@@ -248,16 +310,20 @@ __device__ __forceinline__ int64_t point_at_work(int64_t t, int64_t N, const Div
   return muldiv_ceil(t, N, D);
 }
 
+// y kinds a stream kernel is compiled for: any (dispatch on the plan's type and
+// NaN-aware flag) or one type without the NaN-aware rule.  A kernel specialised to one
+// kind inlines one segment routine instead of four and keeps its state in registers.
+enum YMode : int { kYAny = 0, kYF32 = 1, kYF64 = 2 };
+
 // One warp over the binned points [p_lo, p_hi) of one series.  The warp splits into
 // 32/G groups of G lanes (G chosen per series from its mean bin size) and each group
 // works on its own bin, so small bins are processed 32/G at a time.
-template <int kUnroll>
+template <int kUnroll, int kY>
 __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t p_lo,
                                   int64_t p_hi, int64_t w, int lane) {
   const int G = sp.group;
   const int ngroups = 32 / G;
   const int grp = lane / G, gl = lane - grp * G;
-  const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
   const bool ib = sp.binmode == MMLTTB_BINS_INDEX;
   int64_t b = bin_containing(bt, sp, p_lo, lane);
   // index bins: L = floor(mb*nb/B) and rem = mb*nb - L*B for this group's bin mb,
@@ -283,16 +349,23 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
       }
       lo = sb > p_lo ? sb : p_lo;
       hi = sb1 < p_hi ? sb1 : p_hi;
+      if (hi < lo) hi = lo;
     }
-    if (lo < hi) {
+    {  // every group takes part in the group reductions; empty groups have lo == hi
       Record r;
-      if (sp.nan_aware)
-        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G, gmask)
-                                   : segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G, gmask);
-      else
-        r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G, gmask)
-                                   : segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G, gmask);
-      if (gl == 0) bt.rec[sp.bin_off + mb + w] = r;
+      if constexpr (kY == kYF32) {
+        r = segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G);
+      } else if constexpr (kY == kYF64) {
+        r = segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
+      } else {
+        if (sp.nan_aware)
+          r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G)
+                                     : segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G);
+        else
+          r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G)
+                                     : segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
+      }
+      if (gl == 0 && lo < hi) bt.rec[sp.bin_off + mb + w] = r;
     }
     // the round ends with bin b + ngroups - 1 (held by the last group)
     const int64_t last_end = __shfl_sync(kFull, sb1, 31);
@@ -311,7 +384,7 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
 
 
 // Streaming warp w of the launch: every bin piece of every series in its range.
-template <int U>
+template <int U, int kY = kYAny>
 __device__ void stream_warp(const Batch& bt, int64_t w, int lane) {
   int64_t g = warp_begin(w, bt.total_pos, bt.dwarps);
   const int64_t g_end = warp_begin(w + 1, bt.total_pos, bt.dwarps);
@@ -324,7 +397,7 @@ __device__ void stream_warp(const Batch& bt, int64_t w, int lane) {
       // binned points whose work unit lies in [g, seg_end): p0 + q, q in [q_lo, q_hi)
       const int64_t q_lo = point_at_work(g - sp.pos_off, sp.nb, sp.dnpos);
       const int64_t q_hi = point_at_work(seg_end - sp.pos_off, sp.nb, sp.dnpos);
-      if (q_hi > q_lo) warp_series_range<U>(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
+      if (q_hi > q_lo) warp_series_range<U, kY>(bt, sp, sp.p0 + q_lo, sp.p0 + q_hi, w, lane);
       g = seg_end;
     }
     ++s;
