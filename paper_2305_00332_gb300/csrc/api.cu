@@ -311,7 +311,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   bt.n_warps = p.W;
   set_warp_divs(bt);
   bt.total_edges = (p.B > 0 && sp.binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
-  bt.total_slots = p.tab_cap;
+  bt.total_slots = p.tab_cap;  // k_tables: one slot per position
   bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
   bt.edges = p.off_edges ? (int64_t*)(w + p.off_edges) : nullptr;
   bt.partial = p.off_partial ? (double*)(w + p.off_partial) : nullptr;

@@ -83,9 +83,14 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
       if (max_bucket(mcap, K) <= kTableMaxBucket) {
         sp.engine = EN_TABLES;
         sp.tab_cap = mcap;
+        // one table byte per position, 16-byte aligned and padded; the slots of
+        // k_tables are these positions
         b->tab_byte_off[s] = slots;
-        slots += (mcap + 15) & ~int64_t(15);  // 16-byte aligned, padded storage
+        slots += (mcap + 15) & ~int64_t(15);
         if (mcap > b->max_tab) b->max_tab = mcap;
+        int lgS = 0;
+        while ((int64_t(1) << lgS) < max_bucket(mcap, K)) ++lgS;
+        sp.tab_lgS = lgS;
       } else {
         sp.engine = EN_BLOCK;
         b->any_block = true;

@@ -177,6 +177,21 @@ __device__ inline int upper_index(const int64_t* offs, int count, int64_t v) {
   return lo;
 }
 
+// The same, warp-collective (every lane passes the same v): a 32-ary search, two or
+// three rounds of parallel loads for a few thousand entries.
+__device__ inline int warp_upper_index(const int64_t* offs, int count, int64_t v, int lane) {
+  int lo = 0, hi = count;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int q = lo + lane * step;
+    const unsigned le = __ballot_sync(kFull, q < hi && offs[q] <= v);  // a prefix of the lanes
+    const int last = lo + (31 - __clz(le)) * step;
+    hi = last + step < hi ? last + step : hi;
+    lo = last;
+  }
+  return lo;
+}
+
 // floor(a*b/c) for a, b >= 0, c > 0, exact for any int64 inputs whose quotient fits.
 __host__ __device__ inline int64_t muldiv(int64_t a, int64_t b, int64_t c) {
 #ifdef __CUDA_ARCH__

@@ -5,9 +5,8 @@
 //   k_bins     one thread per bin: combine the bin's records (consecutive slots)
 //              into (lower, higher) of argmin/argmax, -1 for an empty bin; each CTA
 //              writes how many indices its bins emit.
-//   k_binscan  one CTA: exclusive scan of the CTA totals, restarted at every
-//              series; the last CTA of a series fixes its count m and the first
-//              and last entries of its preselected list.
+//   k_binscan  one warp per series: exclusive scan of the series' CTA totals; the
+//              series' count m and the first and last entries of its list.
 //   k_place    one thread per bin: block scan + CTA offset place the bin's indices
 //              (and, before LTTB, their x and y as FP64) in the preselected list.
 #include "compact.cuh"
@@ -45,51 +44,33 @@ __global__ void __launch_bounds__(kBinsPerCta) k_bins(const __grid_constant__ Ba
   }
 }
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;
 
+// One warp per series: exclusive scan of the series' CTA totals, 32 at a time with
+// shuffles, then the series' count m and the ends of its list (finish_series).
 __global__ void __launch_bounds__(kScanThreads) k_binscan(const __grid_constant__ Batch bt) {
-  __shared__ int64_t s_inc[kScanThreads];
-  __shared__ int s_head[kScanThreads];
   pdl_wait();
   pdl_trigger();
-  const int tid = threadIdx.x;
-  const int64_t total = bt.total_bin_ctas;
-  int64_t carry = 0;  // running sum of the segment that continues into the next tile
-  for (int64_t tile = 0; tile < total; tile += kScanThreads) {
-    const int64_t c = tile + tid;
-    const bool valid = c < total;
-    const int s = valid ? bt.cta_series[c] : -1;
-    const int64_t v = valid ? bt.cta_sum[c] : 0;
-    const bool head = valid && (c == 0 || bt.cta_series[c - 1] != s);
-    s_inc[tid] = v;
-    s_head[tid] = head ? tid : -1;
-    __syncthreads();
-    // Hillis-Steele inclusive sum and max-scan of segment heads over the tile
-    for (int d = 1; d < kScanThreads; d <<= 1) {
-      const int64_t a = tid >= d ? s_inc[tid - d] : 0;
-      const int h = tid >= d ? s_head[tid - d] : -1;
-      __syncthreads();
-      s_inc[tid] += a;
-      if (h > s_head[tid]) s_head[tid] = h;
-      __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t s = ((int64_t)blockIdx.x * kScanThreads + threadIdx.x) >> 5;
+  if (s >= bt.n_series) return;
+  const SeriesPlan& sp = plan_of(bt, (int)s);
+  if (!binned(sp.branch)) return;
+  const int64_t c0 = sp.bincta_off, c1 = c0 + (sp.B + kBinsPerCta - 1) / kBinsPerCta;
+  int64_t carry = 0;
+  for (int64_t c = c0; c < c1; c += 32) {
+    const int64_t ci = c + lane;
+    const int64_t v = ci < c1 ? (int64_t)bt.cta_sum[ci] : 0;
+    int64_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t t = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += t;
     }
-    const int start = s_head[tid];  // this element's segment start in the tile, or -1
-    int64_t excl = s_inc[tid] - v;
-    if (start >= 0) excl -= start > 0 ? s_inc[start - 1] : 0;
-    else excl += carry;
-    const int last = (int)((total - tile < kScanThreads ? total - tile : kScanThreads) - 1);
-    const int last_start = s_head[last];
-    const int64_t new_carry = last_start >= 0
-                                  ? s_inc[last] - (last_start > 0 ? s_inc[last_start - 1] : 0)
-                                  : carry + s_inc[last];
-    if (valid) {
-      bt.cta_off[c] = excl;
-      const bool tail = c + 1 == total || bt.cta_series[c + 1] != s;
-      if (tail) finish_series(plan_of(bt, s), excl + v);
-    }
-    __syncthreads();
-    carry = new_carry;
+    if (ci < c1) bt.cta_off[ci] = carry + inc - v;
+    carry += __shfl_sync(kFull, inc, 31);
   }
+  if (lane == 0) finish_series(sp, carry);
 }
 
 __global__ void __launch_bounds__(kBinsPerCta) k_place(const __grid_constant__ Batch bt) {
@@ -119,7 +100,8 @@ cudaError_t launch_compact(const Batch& bt, cudaStream_t st) {
   const dim3 grid((unsigned)bt.total_bin_ctas);
   cudaError_t e = launch_pdl(k_bins, grid, dim3(kBinsPerCta), 0, st, bt);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_binscan, dim3(1), dim3(kScanThreads), 0, st, bt);
+  const int64_t scan_ctas = ((int64_t)bt.n_series * 32 + kScanThreads - 1) / kScanThreads;
+  e = launch_pdl(k_binscan, dim3((unsigned)scan_ctas), dim3(kScanThreads), 0, st, bt);
   if (e != cudaSuccess) return e;
   return launch_pdl(k_place, grid, dim3(kBinsPerCta), 0, st, bt);
 }

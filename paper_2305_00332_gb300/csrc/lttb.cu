@@ -14,10 +14,22 @@ constexpr int kChainThreads = 512;
 constexpr int64_t kChainSmemMax = 160 * 1024;  // tables staged in shared memory up to this size
 constexpr int kTableThreads = 64;  // small CTAs: the positions spread over every SM
 
+// One thread per table slot (one slot per position); the warp finds the series of
+// its first slot with a 32-ary search and a lane moves on only where a series ends
+// inside the warp.
 __global__ void __launch_bounds__(kTableThreads) k_tables(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
-  table_entry(bt, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, threadIdx.x & 31);
+  const int lane = threadIdx.x & 31;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t base = slot - lane;
+  if (base >= bt.total_slots) return;
+  int s = 0;
+  if (bt.tab_offs) {
+    s = warp_upper_index(bt.tab_offs, bt.n_series, base, lane);
+    while (s + 1 < bt.n_series && bt.tab_offs[s + 1] <= slot) ++s;
+  }
+  table_entry(bt, slot, s, lane);
 }
 
 __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ Batch bt) {

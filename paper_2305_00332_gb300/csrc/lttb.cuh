@@ -5,7 +5,7 @@
 // LTTB is a chain: the pick b_j of bucket j depends on the pick of bucket j-1.  When
 // buckets are small (MinMaxLTTB puts about r_ps points in each), the chain is cut
 // into independent pieces:
-//   table_entry    every position p that can be the previous pick of bucket j (p in
+//   bucket_pick    every position p that can be the previous pick of bucket j (p in
 //                  bucket j-1, or p = 0 for j = 0) gets T[p] = the offset in bucket j
 //                  of the point with the largest area against p and the mean of
 //                  bucket j+1.  Each area is the same FP64 expression the sequential
@@ -73,17 +73,16 @@ __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N,
   }
 }
 
-// Table entry of slot `slot` of the launch's table-slot space.  Warp-collective: all
-// 32 lanes call it together (lanes without an entry pass any slot; they only take
-// part in the shared-mean exchange).  Lanes that target the same bucket of the same
-// series share its next-bucket mean: the lowest such lane computes it (R7).
-__device__ void table_entry(const Batch& bt, int64_t slot, int lane) {
+// Table entry of slot `slot` of the launch's table-slot space (one slot per position
+// of every series, series s holding slots from tab_offs[s]).  Warp-collective: all 32
+// lanes call it together (lanes without an entry pass any slot; they only take part
+// in the shared-mean exchange).  Lanes that target the same bucket of the same series
+// share its next-bucket mean: the lowest such lane computes it (R7).
+__device__ void table_entry(const Batch& bt, int64_t slot, int s, int lane) {
   bool work = slot < bt.total_slots;
-  int s = 0;
   int64_t p = 0, m = 0, K = 0, N = 0, jt = 0;
   const SeriesPlan* spp = nullptr;
   if (work) {
-    s = bt.tab_offs ? upper_index(bt.tab_offs, bt.n_series, slot) : 0;
     spp = &plan_of(bt, s);
     p = slot - spp->tab_off;
     work = spp->engine == EN_TABLES;
