@@ -57,6 +57,13 @@ def load(path=None):
     lib.mmo_m4.argtypes = [vp, cint, vp, cint, i64, i64, cint, vp]
     lib.mmo_minmaxlttb.restype = i64
     lib.mmo_minmaxlttb.argtypes = [vp, cint, vp, cint, i64, i64, i32, cint, vp]
+    dbl = ctypes.c_double
+    lib.mmo_raster.restype = i64
+    lib.mmo_raster.argtypes = [vp, cint, vp, cint, i64, vp, i64, dbl, dbl, dbl, dbl, cint, cint, vp]
+    lib.mmo_raster_intensity.restype = None
+    lib.mmo_raster_intensity.argtypes = [vp, i64, vp]
+    lib.mmo_visual_counts.restype = None
+    lib.mmo_visual_counts.argtypes = [vp, vp, cint, cint, cint, vp]
     return lib
 
 
@@ -150,6 +157,38 @@ class Oracle:
         m = self._rc(self.lib.mmo_minmaxlttb(y.ctypes.data, yd, xp, xk, len(y), n_out, r_ps,
                                              self._bm(binmode), out.ctypes.data), "minmaxlttb")
         return out[:m].copy()
+
+
+    def raster(self, y, extents, width, height, x=None, idx=None, mask=None):
+        """Sample masks (uint32, height x width) of the line chart through points idx
+        (all points when None), R19; extents = (x0, x1, y0, y1)."""
+        y, yd = self._y(y)
+        x, xk, xp = self._x(x, len(y))
+        if mask is None:
+            mask = np.zeros((height, width), np.uint32)
+        ip, k = None, 0
+        if idx is not None:
+            idx = np.ascontiguousarray(idx, dtype=np.int64)
+            ip, k = idx.ctypes.data, len(idx)
+        x0, x1, y0, y1 = (float(v) for v in extents)
+        self._rc(self.lib.mmo_raster(y.ctypes.data, yd, xp, xk, len(y), ip, k, x0, x1, y0, y1,
+                                     width, height, mask.ctypes.data), "raster")
+        return mask
+
+    def intensity(self, mask):
+        mask = np.ascontiguousarray(mask, dtype=np.uint32)
+        out = np.empty(mask.shape, np.uint8)
+        self.lib.mmo_raster_intensity(mask.ctypes.data, mask.size, out.ctypes.data)
+        return out
+
+    def visual_counts(self, ref, img, margin=20):
+        """(pixels differing by more than margin, sum of squared differences, mask size)."""
+        ref = np.ascontiguousarray(ref, dtype=np.uint8)
+        img = np.ascontiguousarray(img, dtype=np.uint8)
+        counts = np.zeros(3, np.int64)
+        h, w = ref.shape
+        self.lib.mmo_visual_counts(ref.ctypes.data, img.ctypes.data, w, h, margin, counts.ctypes.data)
+        return tuple(int(v) for v in counts)
 
 
 _default = None

@@ -20,7 +20,7 @@
  *   - LTTB: per bucket B_i, the point forming the largest triangle with the
  *     point selected in B_{i-1} and the average (mean x, mean y) of B_{i+1}.
  *
- * Readings where the paper is silent (numbered R1..R18 wherever they are cited):
+ * Readings where the paper is silent (numbered R1..R21 wherever they are cited):
  *   R1  LTTB buckets: first and last point fixed, K = n_out-2 buckets over the
  *       interior positions 1..m-2, bucket j = [floor(j(m-2)/K)+1, floor((j+1)(m-2)/K)+1)
  *       in exact integer arithmetic.
@@ -57,6 +57,21 @@
  *   R18 NaN-aware MinMax / M4 (binmode | NAN_AWARE): a bin that holds a NaN reports
  *       its first NaN as both argmin and argmax (the convention of numpy's argmin and
  *       argmax); other bins as R8.  Plain MinMax/LTTB keep R11.
+ *   R19 Line-chart rasterisation (Sec. 3.1 and the caption of fig:vis_repr: linear
+ *       interpolation, lines 2 pixels wide, anti-aliased).  A W x H canvas, pixel
+ *       (c, r) covering [c, c+1) x [r, r+1), row 0 at the top.  A data point maps to
+ *       px = (x - x0) * (W / (x1 - x0)), py = (y1 - y) * (H / (y1 - y0)) in FP64, each
+ *       operation rounded, then rounded to float32 (a zero extent maps to W/2 or H/2).
+ *       Each pixel holds 4 x 4 samples at c + (i + 0.5)/4, r + (k + 0.5)/4; a sample is
+ *       inked when its distance to a segment between consecutive drawn points is at
+ *       most 1 (half the line width), computed in float32 with every operation
+ *       rounded in the order written in raster_sample().  Intensity = round(255 x
+ *       inked samples / 16), i.e. (16ths * 255 + 8) / 16 in integers.
+ *   R20 Conv-mask: the pixels with an inked reference pixel within Chebyshev
+ *       distance 1 (a 3 x 3 dilation of the reference).
+ *   R21 PEM_20 = (pixels whose intensities differ by more than 20) / |mask|;
+ *       MSE = (sum over all pixels of the squared intensity difference) / |mask|; both
+ *       0 for an empty mask.  mmo_visual_counts returns the exact integer counts.
  */
 #include <math.h>
 #include <stdint.h>
@@ -404,4 +419,109 @@ int64_t mmo_m4(const void *y, int ydt, const void *x, int xk, int64_t n, int64_t
     }
     free(first); free(last); free(imin); free(imax); free(vmin); free(vmax); free(hasnan);
     return m;
+}
+
+
+/* ---- line-chart rasterisation and visual metrics (R19-R21) ---------------- */
+
+/* Canvas coordinate of a data value: v -> (v - a) * (size / (b - a)), FP64, then
+   float32; a zero extent maps to the middle.  `flip` maps to (b - v) * ... (rows). */
+static float raster_coord(double v, double a, double b, int size, int flip)
+{
+    double d = b - a;
+    if (d == 0.0) return (float)(0.5 * (double)size);
+    double s = (double)size / d;
+    double t = flip ? (b - v) : (v - a);
+    return (float)(t * s);
+}
+
+/* Whether sample (sx, sy) lies within distance 1 of segment (ax, ay)-(bx, by). */
+static int raster_sample(float sx, float sy, float ax, float ay, float bx, float by)
+{
+    float dx = bx - ax, dy = by - ay;
+    float len2 = dx * dx + dy * dy;
+    float t = 0.0f;
+    if (len2 > 0.0f) {
+        float num = (sx - ax) * dx + (sy - ay) * dy;
+        t = num / len2;
+        if (t < 0.0f) t = 0.0f;
+        if (t > 1.0f) t = 1.0f;
+    }
+    float qx = ax + t * dx, qy = ay + t * dy;
+    float ex = sx - qx, ey = sy - qy;
+    float d2 = ex * ex + ey * ey;
+    return d2 <= 1.0f;
+}
+
+/* Rasterise the polyline through points idx[0..k) of the series (idx NULL: all n
+   points) into `mask`: one 16-bit sample mask per pixel (row-major, W x H), OR-ed
+   into what is already there.  Returns the number of segments drawn. */
+int64_t mmo_raster(const void *y, int ydt, const void *x, int xk, int64_t n, const int64_t *idx,
+                   int64_t k, double x0, double x1, double y0, double y1, int W, int H, uint32_t *mask)
+{
+    if (check_common(y, ydt, x, xk, n) || W <= 0 || H <= 0 || !mask) return MMO_EINVAL;
+    if (!idx) k = n;
+    int64_t segs = 0;
+    for (int64_t q = 0; q + 1 < k; q++) {
+        int64_t ia = idx ? idx[q] : q, ib = idx ? idx[q + 1] : q + 1;
+        float ax = raster_coord(x_at(x, xk, ia), x0, x1, W, 0);
+        float ay = raster_coord(y_at(y, ydt, ia), y0, y1, H, 1);
+        float bx = raster_coord(x_at(x, xk, ib), x0, x1, W, 0);
+        float by = raster_coord(y_at(y, ydt, ib), y0, y1, H, 1);
+        float lox = ax < bx ? ax : bx, hix = ax < bx ? bx : ax;
+        float loy = ay < by ? ay : by, hiy = ay < by ? by : ay;
+        double c0 = floor((double)lox - 1.0), c1 = floor((double)hix + 1.0);
+        double r0 = floor((double)loy - 1.0), r1 = floor((double)hiy + 1.0);
+        if (c0 < 0) c0 = 0;
+        if (r0 < 0) r0 = 0;
+        if (c1 > W - 1) c1 = W - 1;
+        if (r1 > H - 1) r1 = H - 1;
+        for (int64_t r = (int64_t)r0; r <= (int64_t)r1; r++)
+            for (int64_t c = (int64_t)c0; c <= (int64_t)c1; c++) {
+                uint32_t m = 0;
+                for (int kk = 0; kk < 4; kk++)
+                    for (int i = 0; i < 4; i++) {
+                        float sx = (float)c + (0.25f * (float)i + 0.125f);
+                        float sy = (float)r + (0.25f * (float)kk + 0.125f);
+                        if (raster_sample(sx, sy, ax, ay, bx, by)) m |= 1u << (kk * 4 + i);
+                    }
+                mask[r * W + c] |= m;
+            }
+        segs++;
+    }
+    return segs;
+}
+
+/* Intensities of a canvas of sample masks (R19). */
+void mmo_raster_intensity(const uint32_t *mask, int64_t pixels, uint8_t *out)
+{
+    for (int64_t p = 0; p < pixels; p++) {
+        uint32_t v = mask[p] & 0xffffu;
+        int inked = 0;
+        while (v) { inked += (int)(v & 1u); v >>= 1; }
+        out[p] = (uint8_t)((inked * 255 + 8) / 16);
+    }
+}
+
+/* Exact counts behind PEM_margin and MSE (R20, R21): counts[0] = pixels whose
+   intensities differ by more than `margin`, counts[1] = sum of squared differences,
+   counts[2] = conv-mask size. */
+void mmo_visual_counts(const uint8_t *ref, const uint8_t *img, int W, int H, int margin, int64_t *counts)
+{
+    int64_t over = 0, sq = 0, msize = 0;
+    for (int r = 0; r < H; r++)
+        for (int c = 0; c < W; c++) {
+            int d = (int)ref[r * W + c] - (int)img[r * W + c];
+            if (d < 0) d = -d;
+            if (d > margin) over++;
+            sq += (int64_t)d * d;
+            int inmask = 0;
+            for (int rr = r - 1; rr <= r + 1 && !inmask; rr++)
+                for (int cc = c - 1; cc <= c + 1; cc++)
+                    if (rr >= 0 && rr < H && cc >= 0 && cc < W && ref[rr * W + cc] > 0) { inmask = 1; break; }
+            msize += inmask;
+        }
+    counts[0] = over;
+    counts[1] = sq;
+    counts[2] = msize;
 }

@@ -441,6 +441,127 @@ def check_m4(o):
                         assert list(got) == m4_reference(y, m4_members_xwidth(x, n_out // 4)), (n, n_out)
 
 
+# ---- line-chart rasterisation and visual metrics (R19-R21) ----------------------
+
+def _sample_points(c, r):
+    """The 16 sample points of pixel (c, r) as exact fractions, bit index k*4 + i."""
+    from fractions import Fraction as F
+    return [(k * 4 + i, F(c) + F(2 * i + 1, 8), F(r) + F(2 * k + 1, 8)) for k in range(4) for i in range(4)]
+
+
+def _exact_inked(sx, sy, ax, ay, bx, by):
+    """Exact squared distance from a sample to a segment (all Fractions)."""
+    dx, dy = bx - ax, by - ay
+    l2 = dx * dx + dy * dy
+    t = 0
+    if l2 > 0:
+        t = ((sx - ax) * dx + (sy - ay) * dy) / l2
+        t = min(max(t, 0), 1)
+    ex, ey = sx - (ax + t * dx), sy - (ay + t * dy)
+    return ex * ex + ey * ey
+
+
+def check_raster_closed_forms(o):
+    """A horizontal line through the centre of row r inks all 16 samples of row r and
+    8 of rows r-1 and r+1 (sample offsets 1/8, 3/8, 5/8, 7/8 at distances up to 1);
+    a vertical line likewise for columns; intensity (16ths*255+8)/16."""
+    W, H = 10, 7
+    for r in range(1, H - 1):
+        yv = H - (r + 0.5)  # py = (y1 - y) * H/(y1 - y0) with extents (0, W, 0, H)
+        img = o.intensity(o.raster(np.array([yv, yv]), (0, W, 0, H), W, H, x=np.array([0.0, float(W)])))
+        want = np.zeros((H, W), np.uint8)
+        want[r, :] = 255
+        want[r - 1, :] = 128
+        want[r + 1, :] = 128
+        assert np.array_equal(img, want), (r, img)
+    for c in range(1, W - 1):
+        xv = c + 0.5
+        img = o.intensity(o.raster(np.array([0.0, float(H)]), (0, W, 0, H), W, H, x=np.array([xv, xv])))
+        want = np.zeros((H, W), np.uint8)
+        want[:, c] = 255
+        want[:, c - 1] = 128
+        want[:, c + 1] = 128
+        assert np.array_equal(img, want), (c, img)
+    # a sample at distance exactly 1 is inked: a line at py = 3.125 reaches the
+    # samples at sy = 2.125 (row 2 fully inked) and sy = 4.125 (4 samples of row 4)
+    img = o.intensity(o.raster(np.array([H - 3.125] * 2), (0, W, 0, H), W, H, x=np.array([0.0, float(W)])))
+    want = np.zeros((H, W), np.uint8)
+    want[2:4, :] = 255
+    want[4, :] = (4 * 255 + 8) // 16
+    assert np.array_equal(img, want), img
+    # intensity rounding
+    for inked in range(17):
+        m = np.array([[(1 << inked) - 1]], np.uint32)
+        assert int(o.intensity(m)[0, 0]) == (inked * 255 + 8) // 16
+
+
+def check_raster_brute_force(o):
+    """Random short segments with endpoints on a 1/8 grid: every pixel's sample mask
+    equals the exact-arithmetic test (samples within 1e-6 of the boundary excepted,
+    where float rounding may decide)."""
+    from fractions import Fraction as F
+    r = rng(4242)
+    W, H = 12, 9
+    for _ in range(60):
+        a = r.integers(8, 8 * 11, 2)
+        b = a + r.integers(-24, 25, 2)
+        b = np.clip(b, 0, 8 * 11)
+        # with extents (0, W, 0, H): px = x and py = H - y, both exact here
+        xs = np.array([a[0] / 8, b[0] / 8])
+        ys = np.array([H - min(a[1], 8 * H - 1) / 8, H - min(b[1], 8 * H - 1) / 8])
+        got = o.raster(ys, (0, W, 0, H), W, H, x=xs)
+        ax, bx = F(xs[0]), F(xs[1])
+        ay, by = F(H) - F(ys[0]), F(H) - F(ys[1])
+        for rr in range(H):
+            for cc in range(W):
+                for bit, sx, sy in _sample_points(cc, rr):
+                    d2 = _exact_inked(sx, sy, ax, ay, bx, by)
+                    if abs(d2 - 1) < F(1, 10**6):
+                        continue
+                    want = d2 <= 1
+                    have = bool(int(got[rr, cc]) >> bit & 1)
+                    assert want == have, (xs, ys, rr, cc, bit, float(d2))
+
+
+def check_raster_degenerate(o):
+    """No segment for fewer than two points; zero extents map to the canvas middle; a
+    repeated point inks the disc of radius 1 around it (the exact test)."""
+    W, H = 6, 5
+    y = np.array([1.0, 2.0, 3.0])
+    assert not o.raster(y, (0, 2, 0, 4), W, H, idx=np.array([1])).any()
+    assert not o.raster(y[:1], (0, 2, 0, 4), W, H).any()
+    # zero y extent: the line runs through the middle row (py = H/2 = 2.5)
+    img = o.intensity(o.raster(np.array([7.0, 7.0]), (0, W, 7, 7), W, H, x=np.array([0.0, float(W)])))
+    assert np.array_equal(img[2], np.full(W, 255, np.uint8)) and np.array_equal(img[1], np.full(W, 128, np.uint8))
+    from fractions import Fraction as F
+    got = o.raster(np.array([2.5, 2.5]), (0, W, 0, H), W, H, x=np.array([2.5, 2.5]))
+    for rr in range(H):
+        for cc in range(W):
+            for bit, sx, sy in _sample_points(cc, rr):
+                want = (sx - F(5, 2)) ** 2 + (sy - F(5, 2)) ** 2 <= 1
+                assert want == bool(int(got[rr, cc]) >> bit & 1)
+
+
+def check_visual_counts(o):
+    """PEM/MSE counts on hand-made images: identical images differ nowhere; a 3 x 3
+    blob of 255 against a blank image differs in 9 pixels by 255 and its conv-mask is
+    the 5 x 5 square around it; differences of exactly the margin do not count."""
+    W, H = 9, 8
+    ref = np.zeros((H, W), np.uint8)
+    ref[2:5, 3:6] = 255
+    assert o.visual_counts(ref, ref) == (0, 0, 25)
+    assert o.visual_counts(ref, np.zeros_like(ref)) == (9, 9 * 255 * 255, 25)
+    img = ref.copy()
+    img[3, 4] = 255 - 20
+    img[2, 3] = 255 - 21
+    assert o.visual_counts(ref, img) == (1, 20 * 20 + 21 * 21, 25)
+    # a blob at the corner: the mask is clipped to the canvas
+    ref2 = np.zeros((H, W), np.uint8)
+    ref2[0, 0] = 1
+    assert o.visual_counts(ref2, ref2) == (0, 0, 4)
+    assert o.visual_counts(np.zeros_like(ref), ref) == (9, 9 * 255 * 255, 0)
+
+
 ALL_CHECKS = [
     check_worked_examples,
     check_minmax_index_bins,
@@ -454,4 +575,8 @@ ALL_CHECKS = [
     check_m4,
     check_minmax_xwidth_f64,
     check_nan_aware,
+    check_raster_closed_forms,
+    check_raster_brute_force,
+    check_raster_degenerate,
+    check_visual_counts,
 ]

@@ -51,6 +51,15 @@ MUTANTS = [
     ("nan_ignored", "            hasnan[b] = 1; imin[b] = p; imax[b] = p;\n        } else {\n            /* strict",
      "            hasnan[b] = 0;\n        } else {\n            /* strict"),
     ("no_lttb_when_rps_covers_n", "if ((int64_t)r_ps * n_out >= n) return mmo_lttb(y, ydt, x, xk, n, n_out, out);", ""),
+    ("raster_sample_offset", "(0.25f * (float)i + 0.125f)", "(0.25f * (float)i)"),
+    ("raster_strict_width", "return d2 <= 1.0f;", "return d2 < 1.0f;"),
+    ("raster_no_row_flip", "double t = flip ? (b - v) : (v - a);", "double t = (v - a);"),
+    ("raster_no_bbox_margin", "double c0 = floor((double)lox - 1.0), c1 = floor((double)hix + 1.0);",
+     "double c0 = floor((double)lox), c1 = floor((double)hix);"),
+    ("raster_no_clamp", "if (t > 1.0f) t = 1.0f;", ""),
+    ("raster_intensity_floor", "out[p] = (uint8_t)((inked * 255 + 8) / 16);", "out[p] = (uint8_t)((inked * 255) / 16);"),
+    ("pem_margin_inclusive", "if (d > margin) over++;", "if (d >= margin) over++;"),
+    ("mask_no_dilation", "for (int rr = r - 1; rr <= r + 1 && !inmask; rr++)", "for (int rr = r; rr <= r && !inmask; rr++)"),
 ]
 
 
