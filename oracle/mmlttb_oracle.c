@@ -468,14 +468,23 @@ int64_t mmo_raster(const void *y, int ydt, const void *x, int xk, int64_t n, con
         float ay = raster_coord(y_at(y, ydt, ia), y0, y1, H, 1);
         float bx = raster_coord(x_at(x, xk, ib), x0, x1, W, 0);
         float by = raster_coord(y_at(y, ydt, ib), y0, y1, H, 1);
+        segs++;
+        /* A NaN endpoint makes every sample distance NaN, so the segment inks nothing. */
+        if (ax != ax || ay != ay || bx != bx || by != by) continue;
         float lox = ax < bx ? ax : bx, hix = ax < bx ? bx : ax;
         float loy = ay < by ? ay : by, hiy = ay < by ? by : ay;
         double c0 = floor((double)lox - 1.0), c1 = floor((double)hix + 1.0);
         double r0 = floor((double)loy - 1.0), r1 = floor((double)hiy + 1.0);
+        /* clip to the canvas (from both sides, so that far-away coordinates leave an
+           empty range and every value converts to int64) */
         if (c0 < 0) c0 = 0;
         if (r0 < 0) r0 = 0;
+        if (c0 > W) c0 = W;
+        if (r0 > H) r0 = H;
         if (c1 > W - 1) c1 = W - 1;
         if (r1 > H - 1) r1 = H - 1;
+        if (c1 < -1) c1 = -1;
+        if (r1 < -1) r1 = -1;
         for (int64_t r = (int64_t)r0; r <= (int64_t)r1; r++)
             for (int64_t c = (int64_t)c0; c <= (int64_t)c1; c++) {
                 uint32_t m = 0;
@@ -487,7 +496,6 @@ int64_t mmo_raster(const void *y, int ydt, const void *x, int xk, int64_t n, con
                     }
                 mask[r * W + c] |= m;
             }
-        segs++;
     }
     return segs;
 }

@@ -533,6 +533,15 @@ def check_raster_degenerate(o):
     # zero y extent: the line runs through the middle row (py = H/2 = 2.5)
     img = o.intensity(o.raster(np.array([7.0, 7.0]), (0, W, 7, 7), W, H, x=np.array([0.0, float(W)])))
     assert np.array_equal(img[2], np.full(W, 255, np.uint8)) and np.array_equal(img[1], np.full(W, 128, np.uint8))
+    # a NaN point breaks the line: the canvas equals the two parts drawn apart
+    yv = np.array([0.5, 3.0, np.nan, 1.0, 4.5])
+    xv = np.array([0.0, 1.5, 3.0, 4.5, 6.0])
+    both = o.raster(yv[:2], (0, W, 0, H), W, H, x=xv[:2])
+    o.raster(yv[3:], (0, W, 0, H), W, H, x=xv[3:], mask=both)
+    assert np.array_equal(o.raster(yv, (0, W, 0, H), W, H, x=xv), both)
+    # far-away points leave the canvas untouched where the line does not pass
+    far = o.raster(np.array([1e300, -1e300]), (0, W, 0, H), W, H, x=np.array([-1e300, -1e300]))
+    assert not far.any()
     from fractions import Fraction as F
     got = o.raster(np.array([2.5, 2.5]), (0, W, 0, H), W, H, x=np.array([2.5, 2.5]))
     for rr in range(H):
