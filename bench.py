@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="1e9-xwidth",
-                    choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving"],
+                    choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving", "visual"],
                     help="the headline (default) or one of the other measured workloads")
     return ap.parse_args()
 

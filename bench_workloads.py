@@ -10,6 +10,11 @@
   serving       64 resident series of 1e8 float32 points; Poisson zoom-window requests
                 (width log-uniform in [1e4, 1e8], n_out in U{500..4000}, r_ps=4) at several
                 rates; continuous-batching server vs one request per launch; p50/p99.
+  visual        line charts on an 800 x 250 canvas: rasteriser throughput on the chart of
+                all points of a 1e7 float32 walk + sines + spikes; and for a 2e5-point
+                template of the same kind (the reference-image size of the paper's figure)
+                the charts of MinMax, MinMaxLTTB (r_ps 2, 4, 6, 8), LTTB and M4 at n_out
+                200..2000 with their PEM_20 and MSE against the chart of all points.
 """
 import ctypes
 import json
@@ -182,6 +187,66 @@ def run_serving(args, mm):
           {"dtype": "f32", "rates": results, "input_gen_s": round(gen, 1)}, args)
 
 
+def run_visual(args, mm):
+    n, W, H = 10_000_000, 800, 250
+    y_host = synth.walk_sines_spikes(n, seed=0)
+    y = torch.from_numpy(y_host).cuda()
+    ext = (0.0, float(n - 1), float(y_host.min()), float(y_host.max()))
+    mask = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    mm.raster(y, ext, W, H, mask=mask)
+    # OR-ing the same chart into the finished canvas repeats exactly the same work
+    steps = max(5, args.steps // 10)
+    before = mm.launch_count()
+    rmed, rmean = _time_calls(lambda: mm.raster(y, ext, W, H, mask=mask), steps)
+    launches = (mm.launch_count() - before) // (steps + 5)
+    inked = int((mm.intensity(mask) > 0).sum().item())
+    # PEM_20 / MSE table on a 2e5-point template
+    nt = 200_000
+    t_host = synth.walk_sines_spikes(nt, seed=1, periods=(1e2, 1e4, 1e6))
+    yt = torch.from_numpy(t_host).cuda()
+    ext_t = (0.0, float(nt - 1), float(t_host.min()), float(t_host.max()))
+    ref_img = mm.intensity(mm.raster(yt, ext_t, W, H))
+    table = {}
+    methods = [("minmax", lambda k: mm.minmax_preselect(yt, k, 1))]
+    methods += [(f"minmaxlttb_r{r}", (lambda r: lambda k: mm.minmaxlttb(yt, k, r))(r)) for r in (2, 4, 6, 8)]
+    methods += [("lttb", lambda k: mm.lttb(yt, k)), ("m4", lambda k: mm.m4(yt, k))]
+    img_mask = torch.zeros_like(mask)
+    for name, sel_fn in methods:
+        row = {}
+        for n_out in (200, 500, 1000, 2000):
+            sel = sel_fn(n_out)
+            img_mask.zero_()
+            mm.raster(yt, ext_t, W, H, idx=sel, mask=img_mask)
+            m = mm.visual_metrics(ref_img, mm.intensity(img_mask), 20)
+            row[str(n_out)] = {"pem20": round(m["pem"], 5), "mse": round(m["mse"], 2)}
+        table[name] = row
+    chart_ms = {}
+    sel = mm.minmaxlttb(yt, 1000, 4)
+
+    def chart():
+        img_mask.zero_()
+        mm.raster(yt, ext_t, W, H, idx=sel, mask=img_mask)
+        mm.visual_counts(ref_img, mm.intensity(img_mask), 20, sync=False)
+    cmed, _ = _time_calls(chart, args.steps)
+    chart_ms["minmaxlttb_r4_n_out1000_chart_and_metrics_us"] = cmed * 1e3
+    # CPU oracle on a bounded sample: the chart of the first 1e6 points
+    from oracle import oracle
+    o = oracle()
+    S = 1_000_000
+    t = time.perf_counter()
+    o.raster(y_host[:S], ext, W, H)
+    cpu_s = time.perf_counter() - t
+    _line("reference line-chart rasterisation throughput (1e7 points, 800x250, 4x4 samples)",
+          (n - 1) / (rmed * 1e-3) / 1e9, "Gsegments/s", True,
+          {"workload": "line charts 800x250: 1e7-point float32 walk + sines + spikes (throughput); "
+                       "2e5-point template and its downsampled charts, n_out 200..2000 (PEM_20, MSE)"},
+          {"dtype": "f32", "reference_chart_ms": rmed, "reference_chart_ms_back_to_back": rmean,
+           "inked_pixels": inked, "gpu_launches": launches, **chart_ms, "pem20_mse_template_2e5": table,
+           "cpu_baseline": {"value": (S - 1) / cpu_s / 1e9, "unit": "Gsegments/s", "cores": 1,
+                            "kind": "oracle", "sample": f"chart of the first {S} points, single-threaded C oracle"}},
+          args)
+
+
 def run(args):
     import importlib.util
     import os
@@ -192,4 +257,5 @@ def run(args):
     mod.build_library()
     import paper_2305_00332_gb300 as mm
     torch.cuda.set_device(0)
-    {"1e6": run_1e6, "1e8-vs-lttb": run_1e8, "batched-4096": run_batched, "serving": run_serving}[args.workload](args, mm)
+    {"1e6": run_1e6, "1e8-vs-lttb": run_1e8, "batched-4096": run_batched, "serving": run_serving,
+     "visual": run_visual}[args.workload](args, mm)

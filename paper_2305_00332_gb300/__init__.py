@@ -352,6 +352,69 @@ def launch_count():
     return int(lib.mmlttb_launch_count())
 
 
+# ---- line-chart rasterisation and visual metrics (include/mmlttb_raster.h) ----
+_f64 = ctypes.c_double
+lib.mmlttb_raster.argtypes = [_vp, _int, _vp, _int, _i64, _vp, _i64, _f64, _f64, _f64, _f64, _i32, _i32, _vp, _vp]
+lib.mmlttb_raster_intensity.argtypes = [_vp, _i64, _vp, _vp]
+lib.mmlttb_visual_counts.argtypes = [_vp, _vp, _i32, _i32, _i32, _vp, _vp]
+
+
+def raster(y, extents, width, height, x=None, idx=None, mask=None):
+    """Line chart of the points idx (all points when None) of series (x, y) on a
+    width x height canvas (mmlttb_raster): per pixel the 16-bit mask of inked samples,
+    OR-ed into `mask` (an int32 tensor of shape (height, width) holding the uint32 bit
+    patterns; a zeroed one is made when None).  extents = (x0, x1, y0, y1)."""
+    _check_inputs(y, x)
+    if mask is None:
+        mask = torch.zeros((height, width), dtype=torch.int32, device=y.device)
+    elif mask.dtype != torch.int32 or tuple(mask.shape) != (height, width) or not mask.is_contiguous():
+        raise ValueError("mask must be a contiguous int32 tensor of shape (height, width)")
+    ip, k = None, 0
+    if idx is not None:
+        if idx.dtype != torch.int64 or idx.dim() != 1 or not idx.is_contiguous() or idx.device != y.device:
+            raise ValueError("idx must be a contiguous 1-D int64 tensor on the device of y")
+        ip, k = idx.data_ptr(), idx.numel()
+    x0, x1, y0, y1 = (float(v) for v in extents)
+    _check(lib.mmlttb_raster(y.data_ptr(), _ydt(y), x.data_ptr() if x is not None else None, _xkind(x),
+                             y.numel(), ip, k, x0, x1, y0, y1, width, height, mask.data_ptr(),
+                             _stream(y.device)), "mmlttb_raster")
+    return mask
+
+
+def intensity(mask):
+    """8-bit intensities of a canvas of sample masks (mmlttb_raster_intensity)."""
+    if mask.dtype != torch.int32 or not mask.is_contiguous():
+        raise ValueError("mask must be a contiguous int32 tensor")
+    out = torch.empty(mask.shape, dtype=torch.uint8, device=mask.device)
+    _check(lib.mmlttb_raster_intensity(mask.data_ptr(), mask.numel(), out.data_ptr(), _stream(mask.device)),
+           "mmlttb_raster_intensity")
+    return out
+
+
+def visual_counts(ref, img, margin=20, sync=True):
+    """(pixels differing by more than margin, sum of squared differences, conv-mask
+    size) of two 8-bit images of the same shape (mmlttb_visual_counts); with
+    sync=False the device int64[3] tensor."""
+    if ref.dtype != torch.uint8 or img.dtype != torch.uint8 or ref.shape != img.shape or ref.dim() != 2:
+        raise ValueError("ref and img must be uint8 images of the same (height, width)")
+    if not (ref.is_contiguous() and img.is_contiguous()) or ref.device != img.device:
+        raise ValueError("ref and img must be contiguous and on one device")
+    counts = torch.empty(3, dtype=torch.int64, device=ref.device)
+    h, w = ref.shape
+    _check(lib.mmlttb_visual_counts(ref.data_ptr(), img.data_ptr(), w, h, margin, counts.data_ptr(),
+                                    _stream(ref.device)), "mmlttb_visual_counts")
+    if not sync:
+        return counts
+    return tuple(int(v) for v in counts.tolist())
+
+
+def visual_metrics(ref, img, margin=20):
+    """PEM_margin and MSE of img against the reference image ref, both over the
+    conv-mask of ref (0 for an empty mask)."""
+    over, sq, size = visual_counts(ref, img, margin)
+    return {"pem": over / size if size else 0.0, "mse": sq / size if size else 0.0, "mask": size}
+
+
 lib.mmlttb_set_single_path.argtypes = [_int]
 lib.mmlttb_single_path.argtypes = [_int, _int, _int, _i64, _i64, _i32, _int]
 

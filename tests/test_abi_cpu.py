@@ -1,5 +1,5 @@
 """The C ABI without a GPU: the library loads, exports every entry point that
-include/mmlttb.h declares, and rejects bad arguments on the host before it would
+include/*.h declares, and rejects bad arguments on the host before it would
 touch a device (no compute calls here)."""
 import ctypes
 import os
@@ -9,13 +9,16 @@ import pytest
 
 from conftest import ROOT
 
-HEADER = os.path.join(ROOT, "include", "mmlttb.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mmlttb_\w+)\s*\(", text)))
+    names = set()
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, f)).read(), flags=re.S)
+            names.update(re.findall(r"\b(mmlttb_\w+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +29,8 @@ def lib(libpath):
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for required in ("mmlttb_minmax_preselect", "mmlttb_lttb", "mmlttb_minmaxlttb",
-                     "mmlttb_workspace_bytes", "mmlttb_strerror"):
+                     "mmlttb_workspace_bytes", "mmlttb_strerror", "mmlttb_raster",
+                     "mmlttb_raster_intensity", "mmlttb_visual_counts"):
         assert required in names
 
 
@@ -78,3 +82,44 @@ def test_single_path_preference_is_validated_on_the_host(lib):
         assert f(bad) == -1
     for good in (1, 2, 3, 0):  # ends on AUTO
         assert f(good) == 0
+
+
+def _raster(lib, y=1, ydt=0, x=None, xk=0, n=10, idx=None, k=0, ext=(0.0, 1.0, 0.0, 1.0), w=8, h=8, mask=1):
+    f = lib.mmlttb_raster
+    f.restype = ctypes.c_int
+    d = ctypes.c_double
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_int64, d, d, d, d, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    return f(y, ydt, x, xk, n, idx, k, *ext, w, h, mask, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(y=None), dict(mask=None), dict(ydt=3), dict(xk=5), dict(xk=1), dict(n=-1), dict(idx=1, k=-2),
+    dict(ext=(0.0, float("inf"), 0.0, 1.0)), dict(ext=(0.0, 1.0, float("nan"), 1.0)), dict(w=0), dict(h=-3),
+    dict(w=65537), dict(w=65536, h=8192),
+])
+def test_raster_validation(lib, kw):
+    assert _raster(lib, **kw) == -1
+
+
+def test_raster_with_fewer_than_two_points_enqueues_nothing(lib):
+    # returns before any CUDA call: fake pointers are never touched
+    assert _raster(lib, n=1) == 0
+    assert _raster(lib, idx=1, k=1) == 0
+    assert _raster(lib, n=0, ext=(5.0, -5.0, 2.0, 2.0)) == 0  # reversed / zero extents are valid
+
+
+def test_visual_metric_validation(lib):
+    f = lib.mmlttb_visual_counts
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    assert f(None, 1, 4, 4, 20, 1, None) == -1
+    assert f(1, 1, 0, 4, 20, 1, None) == -1
+    assert f(1, 1, 4, 4, -1, 1, None) == -1
+    assert f(1, 1, 4, 4, 20, None, None) == -1
+    assert f(1, 1, 65536, 65536, 20, 1, None) == -1
+    g = lib.mmlttb_raster_intensity
+    g.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    assert g(None, 4, 1, None) == -1
+    assert g(1, -1, 1, None) == -1
+    assert g(1, 0, 1, None) == 0
