@@ -165,7 +165,8 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     const int64_t N = p.branch == BR_M4 ? n : (n > 2 ? n - 2 : 0);
     p.nb = N;
     // x-width bins can be very uneven: keep whole warps per bin there
-    p.group = binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(N, p.B, ydt == MMLTTB_F32 ? 4 : 8);
+    const int eb = ydt == MMLTTB_F32 ? 4 : 8;
+    p.group = binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(N, p.B, eb, N * eb >= kStreamThroughputBytes);
     p.npos = series_work(N, p.B, p.group);
     p.Wcap = stream_warp_cap(d);
     p.variant = stream_variant(d, ydt);

@@ -28,6 +28,10 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
   b->tab_byte_off.assign(n, -1);
   b->mean_off.assign(n, -1);
   int64_t pos = 0, bins = 0, edges = 0, slots = 0, sel = 0, means = 0, ctas = 0;
+  int64_t y_bytes = 0;  // the batch's y, which the stream reads about once
+  for (int64_t s = 0; s < n; ++s)
+    if (b->descs[s].n_in > 0) y_bytes += b->descs[s].n_in * (b->descs[s].ydtype == MMLTTB_F32 ? 4 : 8);
+  const bool throughput = y_bytes >= kStreamThroughputBytes;
   for (int64_t s = 0; s < n; ++s) {
     const mmlttb_series_desc& D = b->descs[s];
     int32_t br;
@@ -64,7 +68,8 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
     sp.p0 = br == BR_M4 ? 0 : 1;
     sp.nb = br == BR_M4 ? D.n_in : (D.n_in > 2 ? D.n_in - 2 : 0);
     // x-width bins can be very uneven: keep whole warps per bin there
-    sp.group = sp.binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(sp.nb, B, D.ydtype == MMLTTB_F32 ? 4 : 8);
+    sp.group = sp.binmode == MMLTTB_BINS_XWIDTH ? 32
+                                                : stream_group(sp.nb, B, D.ydtype == MMLTTB_F32 ? 4 : 8, throughput);
     if (mm) {
       sp.npos = series_work(sp.nb, B, sp.group);
       pos += sp.npos;

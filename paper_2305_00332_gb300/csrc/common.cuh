@@ -140,6 +140,7 @@ struct Batch {
   double* partial;     // 2 x grid x (area, position) partials (EN_GRID)
   int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
   int32_t zero_status; // the launch clears the status and barrier words first (first kernel of a call)
+  int32_t tab_rounds;  // k_tables: rounds of 32 slots per warp (1..kTableRounds)
 };
 
 __host__ __device__ inline void set_bin_steps(SeriesPlan& sp) {
@@ -330,15 +331,22 @@ constexpr int64_t kBinCostMax = 32 * kBinCostPerLane;
 __host__ __device__ inline int64_t series_work(int64_t N, int64_t B, int G) {
   return N > 0 ? N + kBinCostPerLane * G * (B < N ? B : N) : 0;
 }
-// Lanes per bin for a series, a power of two: about 512 bytes (32 loads of 16 bytes)
-// per lane per bin, and at least 2 lanes for bins over 128 bytes.  A bin costs a fixed
-// round of bounds, reduction and record store, so lanes that read more of it
-// amortise that round; measured on 1e8 float32 points, 125-point bins went from 2.5 to
-// 3.3 TB/s and 1024-point bins from 3.2 to 3.8 TB/s against about one load per lane.
-__host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes) {
+// Lanes per bin for a series, a power of two.  A bin costs a fixed round of bounds,
+// reduction and record store.  For launches that stream at least
+// kStreamThroughputBytes the lanes read about 512 bytes (32 loads of 16 bytes) each
+// per bin, at least 2 lanes above 128-byte bins, which amortises that round (on 1e8
+// float32 points: 125-point bins 2.5 -> 3.3 TB/s, 1024-point bins 3.2 -> 3.8 TB/s).
+// Smaller launches are latency-bound: about one 64-byte round trip per lane per bin.
+constexpr int64_t kStreamThroughputBytes = int64_t(64) << 20;
+__host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes, bool throughput) {
   const int64_t per_bin_bytes = (B > 0 ? N / B : N) * elem_bytes;
+  int G = 1;
+  if (!throughput) {
+    while (G < 32 && (int64_t)G * 64 < per_bin_bytes) G <<= 1;
+    return G;
+  }
   if (per_bin_bytes <= 128) return 1;
-  int G = 2;
+  G = 2;
   while (G < 32 && (int64_t)G * 512 < per_bin_bytes) G <<= 1;
   return G;
 }

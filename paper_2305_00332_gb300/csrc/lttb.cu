@@ -14,22 +14,19 @@ constexpr int kChainThreads = 512;
 constexpr int64_t kChainSmemMax = 160 * 1024;  // tables staged in shared memory up to this size
 constexpr int kTableThreads = 64;  // small CTAs: the positions spread over every SM
 
-// One thread per table slot (one slot per position); the warp finds the series of
-// its first slot with a 32-ary search and a lane moves on only where a series ends
-// inside the warp.
+// A warp per kTableBlock consecutive table slots (one slot per position); the warp
+// finds the series of its first slot with a 32-ary search.
 __global__ void __launch_bounds__(kTableThreads) k_tables(const __grid_constant__ Batch bt) {
+  __shared__ TableReq s_req[kTableThreads / 32][kTableBlock];
+  __shared__ double2 s_mean[kTableThreads / 32][kTableBlock];
   pdl_wait();
   pdl_trigger();
-  const int lane = threadIdx.x & 31;
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t base = slot - lane;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rounds = bt.tab_rounds;
+  const int64_t base = ((int64_t)blockIdx.x * (kTableThreads / 32) + wid) * 32 * rounds;
   if (base >= bt.total_slots) return;
-  int s = 0;
-  if (bt.tab_offs) {
-    s = warp_upper_index(bt.tab_offs, bt.n_series, base, lane);
-    while (s + 1 < bt.n_series && bt.tab_offs[s + 1] <= slot) ++s;
-  }
-  table_entry(bt, slot, s, lane);
+  const int s0 = bt.tab_offs ? warp_upper_index(bt.tab_offs, bt.n_series, base, lane) : 0;
+  table_block(bt, base, rounds, s0, lane, s_req[wid], s_mean[wid]);
 }
 
 __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ Batch bt) {
@@ -220,8 +217,18 @@ int lttb_grid_blocks_per_sm() {
 
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st) {
   if (bt.total_slots <= 0) return cudaSuccess;
-  const int64_t grid = (bt.total_slots + kTableThreads - 1) / kTableThreads;
-  return launch_pdl(k_tables, dim3((unsigned)grid), dim3(kTableThreads), 0, st, bt);
+  // as many rounds per warp as keep about 16 warps per SM busy, at most kTableRounds
+  int dev = 0, sms = 152;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  Batch b = bt;
+  const int64_t r = bt.total_slots / ((int64_t)sms * 16 * 32);
+  b.tab_rounds = (int32_t)(r < 1 ? 1 : r > kTableRounds ? kTableRounds : r);
+  const int64_t per_cta = (int64_t)(kTableThreads / 32) * 32 * b.tab_rounds;
+  const int64_t grid = (bt.total_slots + per_cta - 1) / per_cta;
+  return launch_pdl(k_tables, dim3((unsigned)grid), dim3(kTableThreads), 0, st, b);
 }
 
 cudaError_t launch_chain(const Batch& bt, int n_blocks, int64_t max_positions, cudaStream_t st) {

@@ -73,84 +73,132 @@ __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N,
   }
 }
 
-// Table entry of slot `slot` of the launch's table-slot space (one slot per position
-// of every series, series s holding slots from tab_offs[s]).  Warp-collective: all 32
-// lanes call it together (lanes without an entry pass any slot; they only take part
-// in the shared-mean exchange).  Lanes that target the same bucket of the same series
-// share its next-bucket mean: the lowest such lane computes it (R7).
-__device__ void table_entry(const Batch& bt, int64_t slot, int s, int lane) {
-  bool work = slot < bt.total_slots;
-  int64_t p = 0, m = 0, K = 0, N = 0, jt = 0;
-  const SeriesPlan* spp = nullptr;
-  if (work) {
-    spp = &plan_of(bt, s);
-    p = slot - spp->tab_off;
-    work = spp->engine == EN_TABLES;
-    if (work) {
-      m = lttb_m(*spp);
-      work = p < m && m > spp->n_out;
-    }
-    if (work) {
-      K = spp->n_out - 2;
-      N = m - 2;
-      if (p == 0) jt = 0;               // the bucket whose pick follows a pick at p
-      else if (p <= m - 2) jt = part_of(p, N, K) + 1;
-      else work = false;
-      if (jt >= K) work = false;
-    }
+// Slots a warp of k_tables fills: up to kTableRounds rounds of 32 (bt.tab_rounds; one
+// round when there are too few slots to fill the GPU).  The next-bucket means of all
+// the buckets these slots target are formed together, one bucket per lane: an FP64
+// instruction costs the FP64 pipe the same whether one lane or 32 execute it, and a
+// round of 32 positions holds only about 32/r_ps buckets.
+constexpr int kTableRounds = 7;
+constexpr int kTableBlock = 32 * kTableRounds;
+
+struct TableReq {  // a bucket whose next-bucket mean the warp needs
+  int64_t jt;      // the bucket (its picks follow picks in bucket jt - 1)
+  int32_t s;       // series
+  int32_t pad;
+};
+
+// Table slot `slot` (one slot per position of every series, series s holding slots
+// from tab_offs[s]): whether it has an entry, and the bucket jt whose pick follows a
+// pick at its position (R1).
+__device__ __forceinline__ bool slot_bucket(const Batch& bt, int64_t slot, int s, int64_t* jt) {
+  if (slot >= bt.total_slots) return false;
+  const SeriesPlan& sp = plan_of(bt, s);
+  if (sp.engine != EN_TABLES) return false;
+  const int64_t p = slot - sp.tab_off, m = lttb_m(sp);
+  if (p >= m || m <= sp.n_out) return false;
+  const int64_t K = sp.n_out - 2;
+  if (p == 0) {
+    *jt = 0;
+  } else {
+    if (p > m - 2) return false;
+    *jt = part_of(p, m - 2, K) + 1;
   }
-  const unsigned long long key = work ? ((unsigned long long)s << 40) ^ (unsigned long long)jt
-                                      : ~0ull - (unsigned long long)lane;
-  const unsigned group = __match_any_sync(kFull, key);
-  const int leader = __ffs(group) - 1;
-  double xc = 0.0, yc = 0.0, xa = 0.0, ya = 0.0;
-  double xb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
-  int64_t lo = 0, hi = 0;
-  if (work) {
-    const SeriesPlan& sp = *spp;
-    pos_xy(sp, p, &xa, &ya);
-    // bucket jt = [lo, hi) (R1) and the next one, stepped from one division
-    StepDiv bs;
-    bs.init(jt, N, sp.dK, 1);
-    lo = bs.L + 1;
+  return *jt < K;
+}
+
+// Table entries of the warp's block of slots [base, base + 32*rounds).  Warp-
+// collective; `s0` is the series of slot `base`; req/mean are the warp's shared
+// memory (kTableBlock entries each).
+__device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, int lane, TableReq* req,
+                            double2* mean) {
+  // 1. every slot's bucket; the first slot of each distinct (series, bucket) files a
+  //    request, and every slot keeps the index of its bucket's request
+  int dreq[kTableRounds];
+  int s = s0, nreq = 0;
+  int64_t carry_jt = -1;
+  int carry_s = -1;
+#pragma unroll
+  for (int r = 0; r < kTableRounds; ++r) {
+    dreq[r] = -1;
+    if (r >= rounds) continue;
+    const int64_t slot = base + 32 * r + lane;
+    if (bt.tab_offs)
+      while (s + 1 < bt.n_series && bt.tab_offs[s + 1] <= slot) ++s;
+    int64_t jt = -1;
+    const bool work = slot_bucket(bt, slot, s, &jt);
+    const int ks = work ? s : -1;
+    int64_t pjt = __shfl_up_sync(kFull, work ? jt : -1, 1);
+    int ps = __shfl_up_sync(kFull, ks, 1);
+    if (lane == 0) {
+      pjt = carry_jt;
+      ps = carry_s;
+    }
+    const bool first = work && (ps != ks || pjt != jt);
+    const unsigned fl = __ballot_sync(kFull, first);
+    const int d = nreq + __popc(fl & ((2u << lane) - 1u)) - 1;
+    if (first) {
+      req[d].jt = jt;
+      req[d].s = ks;
+    }
+    dreq[r] = work ? d : -1;
+    nreq += __popc(fl);
+    carry_jt = __shfl_sync(kFull, work ? jt : -1, 31);
+    carry_s = __shfl_sync(kFull, ks, 31);
+  }
+  __syncwarp();
+  // 2. the means, one bucket per lane (R5, R7)
+  for (int d = lane; d < nreq; d += 32) {
+    const TableReq q = req[d];
+    const SeriesPlan& sp = plan_of(bt, q.s);
+    const int64_t m = lttb_m(sp), K = sp.n_out - 2;
+    int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point
+    if (q.jt + 1 < K) {
+      nlo = part_start(q.jt + 1, m - 2, sp.dK);
+      nhi = part_start(q.jt + 2, m - 2, sp.dK);
+    }
+    double xc, yc;
+    bucket_mean(sp, nlo, nhi, &xc, &yc);
+    mean[d] = make_double2(xc, yc);
+  }
+  __syncwarp();
+  // 3. each slot's entry: the first largest area in bucket jt against its position
+#pragma unroll 1
+  for (int r = 0; r < rounds; ++r) {
+    const int d = dreq[r];
+    if (d < 0) continue;
+    const TableReq q = req[d];
+    const SeriesPlan& sp = plan_of(bt, q.s);
+    const int64_t p = base + 32 * r + lane - sp.tab_off;
+    const int64_t m = lttb_m(sp);
+    StepDiv bs;  // bucket jt = [lo, hi) (R1)
+    bs.init(q.jt, m - 2, sp.dK, 1);
+    const int64_t lo = bs.L + 1;
     bs.next();
-    hi = bs.L + 1;
+    const int64_t hi = bs.L + 1;
+    double xa, ya;
+    pos_xy(sp, p, &xa, &ya);
+    const double2 c = mean[d];
+    long long best = -1;  // bits of a non-negative double order like the double
+    int pick = 0;
+    for (int64_t q0 = lo; q0 < hi; q0 += 4) {  // four candidates' loads in flight
+      double xb[4], yb[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)  // the first candidates load while the mean is formed
-      if (lo + u < hi) pos_xy(sp, lo + u, &xb[u], &yb[u]);
-    if (lane == leader) {
-      int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point (R5)
-      if (jt + 1 < K) {
-        nlo = hi;
-        bs.next();
-        nhi = bs.L + 1;
-      }
-      bucket_mean(sp, nlo, nhi, &xc, &yc);
-    }
-  }
-  xc = __shfl_sync(kFull, xc, leader);
-  yc = __shfl_sync(kFull, yc, leader);
-  if (!work) return;
-  const SeriesPlan& sp = *spp;
-  long long best = -1;  // bits of a non-negative double order like the double
-  int pick = 0;
-  for (int64_t q0 = lo; q0 < hi; q0 += 4) {  // four candidates' loads in flight
-    if (q0 > lo) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u) {
+        xb[u] = yb[u] = 0.0;
         if (q0 + u < hi) pos_xy(sp, q0 + u, &xb[u], &yb[u]);
-    }
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (q0 + u >= hi) break;
-      const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], xc, yc));
-      if (q0 + u == lo || ab > best) {  // R8: the first largest wins
-        best = ab;
-        pick = (int)(q0 + u - lo);
+      for (int u = 0; u < 4; ++u) {
+        if (q0 + u >= hi) break;
+        const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], c.x, c.y));
+        if (q0 + u == lo || ab > best) {  // R8: the first largest wins
+          best = ab;
+          pick = (int)(q0 + u - lo);
+        }
       }
     }
+    sp.tab[p] = (uint8_t)pick;
   }
-  sp.tab[p] = (uint8_t)pick;
 }
 
 // The LTTB pick that follows the k-th position of bucket j-1 (position 0 for j = 0):
