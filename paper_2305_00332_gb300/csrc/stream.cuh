@@ -166,53 +166,60 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
   uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
-  const uintptr_t aend = ybase + (uintptr_t)hi * 4u;
-  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
-  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 4 - lo);  // in [-3, 0]
+  const int32_t rel0 = (int32_t)((int64_t)(a0 - ybase) / 4 - lo);  // offset of vector 0's first element: -3..0
   const float4* vp = (const float4*)a0;
-  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
+  // vectors 0..nvec-1 cover the piece; those in [vf, vl) lie wholly inside it, the
+  // others (the first when the piece starts mid-vector, the last when it ends
+  // mid-vector) are masked
+  const int32_t span = (int32_t)len - rel0;
+  const int32_t nvec = len ? (span + 3) >> 2 : 0;
+  const int32_t vf = rel0 < 0 ? 1 : 0, vl = span >> 2;
+  // one vector with its out-of-piece elements masked out (in offset order)
+  auto masked = [&](const float4 b, int32_t r) {
+    const float e[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if ((uint32_t)(r + k) >= len) continue;
+      if (kNanAware && onan == 0xffffffffu && e[k] != e[k]) onan = (uint32_t)(r + k);
+      if (e[k] < mn) { mn = e[k]; omn = (uint32_t)(r + k); }
+      if (e[k] > mx) { mx = e[k]; omx = (uint32_t)(r + k); }
+    }
+  };
+  if (gl == 0 && vf == 1 && nvec > 0) masked(ld_stream4(vp), rel0);  // the lowest offsets first
+  for (int32_t v = vf + gl; v < vl; v += G * kUnroll) {
     float4 buf[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + G * u;
-      if (vi < nvec) buf[u] = ld_stream4(vp + vi);
-    }
+    for (int u = 0; u < kUnroll; u++)
+      if (v + G * u < vl) buf[u] = ld_stream4(vp + (v + G * u));
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + G * u;
-      if (vi < nvec) {
-        const int32_t r = rel0 + 4 * (int32_t)vi;
-        const float e[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
-        float fm[4], fx[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const bool ok = (uint32_t)(r + k) < len;
-          fm[k] = ok ? e[k] : inf;
-          fx[k] = ok ? e[k] : -inf;
+      if (v + G * u >= vl) break;
+      const float4 b = buf[u];
+      if (kNanAware && onan == 0xffffffffu) {
+        if ((b.x != b.x) | (b.y != b.y) | (b.z != b.z) | (b.w != b.w)) {
+          const int32_t r = rel0 + 4 * (v + G * u);
+          onan = (uint32_t)(b.x != b.x ? r : b.y != b.y ? r + 1 : b.z != b.z ? r + 2 : r + 3);
         }
-        if (kNanAware && onan == 0xffffffffu) {
-          const bool any = (e[0] != e[0]) | (e[1] != e[1]) | (e[2] != e[2]) | (e[3] != e[3]);
-          if (any) {
-#pragma unroll
-            for (int k = 3; k >= 0; k--)  // lowest valid NaN of the vector
-              if ((uint32_t)(r + k) < len && e[k] != e[k]) onan = (uint32_t)(r + k);
-          }
-        }
-        const float m4 = fminf(fminf(fm[0], fm[1]), fminf(fm[2], fm[3]));
-        const float x4 = fmaxf(fmaxf(fx[0], fx[1]), fmaxf(fx[2], fx[3]));
-        if (m4 < mn) {  // rare: some element is a new strict minimum
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (fm[k] < mn) { mn = fm[k]; omn = (uint32_t)(r + k); }
-        }
-        if (x4 > mx) {
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (fx[k] > mx) { mx = fx[k]; omx = (uint32_t)(r + k); }
-        }
+      }
+      const float m4 = fminf(fminf(b.x, b.y), fminf(b.z, b.w));
+      const float x4 = fmaxf(fmaxf(b.x, b.y), fmaxf(b.z, b.w));
+      if (m4 < mn) {  // rare: some element is a new strict minimum
+        const int32_t r = rel0 + 4 * (v + G * u);
+        if (b.x < mn) { mn = b.x; omn = (uint32_t)r; }
+        if (b.y < mn) { mn = b.y; omn = (uint32_t)(r + 1); }
+        if (b.z < mn) { mn = b.z; omn = (uint32_t)(r + 2); }
+        if (b.w < mn) { mn = b.w; omn = (uint32_t)(r + 3); }
+      }
+      if (x4 > mx) {
+        const int32_t r = rel0 + 4 * (v + G * u);
+        if (b.x > mx) { mx = b.x; omx = (uint32_t)r; }
+        if (b.y > mx) { mx = b.y; omx = (uint32_t)(r + 1); }
+        if (b.z > mx) { mx = b.z; omx = (uint32_t)(r + 2); }
+        if (b.w > mx) { mx = b.w; omx = (uint32_t)(r + 3); }
       }
     }
   }
+  if (gl == 0 && nvec - 1 >= vl && nvec - 1 >= vf) masked(ld_stream4(vp + (nvec - 1)), rel0 + 4 * (nvec - 1));
   int wmn = key32(mn), wmx = key32(mx);
   unsigned wo = omn, wx = omx;
   group_arg32(wmn, wo, wmx, wx, G);
@@ -246,46 +253,51 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, i
   uint32_t omn = 0xffffffffu, omx = 0xffffffffu, onan = 0xffffffffu;
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 8u) & ~(uintptr_t)15;
-  const uintptr_t aend = ybase + (uintptr_t)hi * 8u;
-  const int64_t nvec = hi > lo ? (int64_t)((aend - a0 + 15u) >> 4) : 0;
-  const int32_t rel0 = (int32_t)(((int64_t)a0 - (int64_t)ybase) / 8 - lo);  // in [-1, 0]
+  const int32_t rel0 = (int32_t)((int64_t)(a0 - ybase) / 8 - lo);  // offset of vector 0's first element: -1..0
   const float inf = __int_as_float(0x7f800000);
-  for (int64_t v = gl; v < nvec; v += G * kUnroll) {
+  // vectors in [vf, vl) lie wholly inside the piece; a first or last vector that is
+  // only partly inside is masked
+  const int32_t span = (int32_t)len - rel0;
+  const int32_t nvec = len ? (span + 1) >> 1 : 0;
+  const int32_t vf = rel0 < 0 ? 1 : 0, vl = span >> 1;
+  // the two elements of vector b at offsets r, r + 1 (ok0/ok1: inside the piece)
+  auto update = [&](const uint4 b, int32_t r, bool ok0, bool ok1) {
+    const float p0 = proxy_of_hi(b.y), p1 = proxy_of_hi(b.w);
+    const float pm = fmin_nan(ok0 ? p0 : inf, ok1 ? p1 : inf);
+    const float px = fmax_nan(ok0 ? p0 : -inf, ok1 ? p1 : -inf);
+    if (!(pm > pmn) || !(px < pmx)) {  // rare: exact comparison through int64 keys
+      const long long e0 = ((long long)b.y << 32) | b.x;
+      const long long e1 = ((long long)b.w << 32) | b.z;
+      const long long k0 = key64(__longlong_as_double(e0));
+      const long long k1 = key64(__longlong_as_double(e1));
+      if (kNanAware && onan == 0xffffffffu) {  // NaN proxies always take this path
+        const long long m = 0x7fffffffffffffffLL, inf_bits = 0x7ff0000000000000LL;
+        if (ok1 && (e1 & m) > inf_bits) onan = (uint32_t)(r + 1);
+        if (ok0 && (e0 & m) > inf_bits) onan = (uint32_t)r;
+      }
+      if (ok0 && k0 < kmn) { kmn = k0; omn = (uint32_t)r; pmn = p0; }
+      if (ok1 && k1 < kmn) { kmn = k1; omn = (uint32_t)(r + 1); pmn = p1; }
+      if (ok0 && k0 > kmx) { kmx = k0; omx = (uint32_t)r; pmx = p0; }
+      if (ok1 && k1 > kmx) { kmx = k1; omx = (uint32_t)(r + 1); pmx = p1; }
+    }
+  };
+  auto masked = [&](int32_t vi) {
+    const int32_t r = rel0 + 2 * vi;
+    update(ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u)), r, (uint32_t)r < len, (uint32_t)(r + 1) < len);
+  };
+  if (gl == 0 && vf == 1 && nvec > 0) masked(0);  // the lowest offsets first
+  for (int32_t v = vf + gl; v < vl; v += G * kUnroll) {
     uint4 buf[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + G * u;
-      if (vi < nvec) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u));
-    }
+    for (int u = 0; u < kUnroll; u++)
+      if (v + G * u < vl) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)(v + G * u) * 16u));
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
-      int64_t vi = v + G * u;
-      if (vi < nvec) {
-        const int32_t r = rel0 + 2 * (int32_t)vi;
-        const bool ok0 = (uint32_t)r < len, ok1 = (uint32_t)(r + 1) < len;
-        const float p0 = proxy_of_hi(buf[u].y), p1 = proxy_of_hi(buf[u].w);
-        const float pm = fmin_nan(ok0 ? p0 : inf, ok1 ? p1 : inf);
-        const float px = fmax_nan(ok0 ? p0 : -inf, ok1 ? p1 : -inf);
-        const bool need_min = !(pm > pmn);
-        const bool need_max = !(px < pmx);
-        if (need_min || need_max) {  // rare: exact comparison through int64 keys
-          const long long e0 = ((long long)buf[u].y << 32) | buf[u].x;
-          const long long e1 = ((long long)buf[u].w << 32) | buf[u].z;
-          const long long k0 = key64(__longlong_as_double(e0));
-          const long long k1 = key64(__longlong_as_double(e1));
-          if (kNanAware && onan == 0xffffffffu) {  // NaN proxies always take this path
-            const long long m = 0x7fffffffffffffffLL, inf_bits = 0x7ff0000000000000LL;
-            if (ok1 && (e1 & m) > inf_bits) onan = (uint32_t)(r + 1);
-            if (ok0 && (e0 & m) > inf_bits) onan = (uint32_t)r;
-          }
-          if (ok0 && k0 < kmn) { kmn = k0; omn = (uint32_t)r; pmn = p0; }
-          if (ok1 && k1 < kmn) { kmn = k1; omn = (uint32_t)(r + 1); pmn = p1; }
-          if (ok0 && k0 > kmx) { kmx = k0; omx = (uint32_t)r; pmx = p0; }
-          if (ok1 && k1 > kmx) { kmx = k1; omx = (uint32_t)(r + 1); pmx = p1; }
-        }
-      }
+      if (v + G * u >= vl) break;
+      update(buf[u], rel0 + 2 * (v + G * u), true, true);
     }
   }
+  if (gl == 0 && nvec - 1 >= vl && nvec - 1 >= vf) masked(nvec - 1);
   unsigned wo = omn, wx = omx;
   group_arg64(kmn, wo, kmx, wx, G);
   Record r;
@@ -302,6 +314,26 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, i
     }
   }
   return r;
+}
+
+// The segment routine for the plan's y type and NaN rule, for kernels compiled for
+// any y.  Each routine stays a separate function: inlined together, the four of
+// them spill their state.
+template <int kUnroll, bool kNan>
+__device__ __noinline__ Record segment_f32_call(const float* y, int64_t lo, int64_t hi, int gl, int G) {
+  return segment_f32<kUnroll, kNan>(y, lo, hi, gl, G);
+}
+template <int kUnroll, bool kNan>
+__device__ __noinline__ Record segment_f64_call(const double* y, int64_t lo, int64_t hi, int gl, int G) {
+  return segment_f64<kUnroll, kNan>(y, lo, hi, gl, G);
+}
+template <int kUnroll>
+__device__ __forceinline__ Record segment_any(const SeriesPlan& sp, int64_t lo, int64_t hi, int gl, int G) {
+  if (sp.nan_aware)
+    return sp.ydt == MMLTTB_F32 ? segment_f32_call<kUnroll, true>((const float*)sp.y, lo, hi, gl, G)
+                                : segment_f64_call<kUnroll, true>((const double*)sp.y, lo, hi, gl, G);
+  return sp.ydt == MMLTTB_F32 ? segment_f32_call<kUnroll, false>((const float*)sp.y, lo, hi, gl, G)
+                              : segment_f64_call<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
 }
 
 // Smallest interior point q in [0, N] whose work unit floor(q*D/N) is >= t, for
@@ -358,12 +390,7 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
       } else if constexpr (kY == kYF64) {
         r = segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
       } else {
-        if (sp.nan_aware)
-          r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G)
-                                     : segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G);
-        else
-          r = (sp.ydt == MMLTTB_F32) ? segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G)
-                                     : segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
+        r = segment_any<kUnroll>(sp, lo, hi, gl, G);
       }
       if (gl == 0 && lo < hi) bt.rec[sp.bin_off + mb + w] = r;
     }
