@@ -145,7 +145,7 @@ def run_serving(args, mm):
     ys = [torch.from_numpy(synth.random_walk(n, seed=5000 + i, dtype=np.float32)).cuda() for i in range(S)]
     gen = time.time() - t
     rng = np.random.default_rng(0)
-    rates = [1000, 5000, 10000, 20000, 50000]
+    rates = [1000, 5000, 10000, 20000, 50000, 100000, 150000]
     duration = 1.0
     results = {}
 
@@ -173,6 +173,8 @@ def run_serving(args, mm):
                 srv.wait(i)
         for rate in rates:
             reqs, offs = trace(rate)
+            if mode == "per_request" and rate > 50000:
+                continue  # saturated near 1e4 req/s: these traces would only queue
             srv.reset_stats()
             t0 = time.perf_counter()
             ids, st = srv.replay(reqs, offs)
