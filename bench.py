@@ -61,6 +61,23 @@ def dist_init(args):
     return ws, rank, local
 
 
+def max_over_ranks(v, ws, device=None):
+    """The largest value of v over the ranks (every rank receives it); v when alone."""
+    if ws <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points_per_rank, ws, seconds):
+    """Whole-job rate in Gpts/s: the points of all ranks (replicas) over the slowest
+    rank's time."""
+    return ws * points_per_rank / seconds / 1e9
+
+
 def make_inputs(n, pinned):
     """Seeded cfg: x int64 exponential gaps, y float64 walk, filled in place."""
     import torch
@@ -247,11 +264,7 @@ def main():
         torch.distributed.barrier()
     time.sleep(0.2)
     clocks.stop()
-    ms = e0.elapsed_time(e1) / K
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / K, ws, dev)
     kern_ms = [a.elapsed_time(b) for a, b in k_ev]
     kern_avg = sum(kern_ms) / len(kern_ms)
     clk = clocks.summary(t_wall0, t_wall1)
@@ -309,16 +322,12 @@ def main():
         for _ in range(E):
             r = mm.minmaxlttb_host(y_h, N_OUT, R_PS, x=x_h, binmode="xwidth", out=out_h,
                                    device_buffer=dbuf, device=dev)
-        el = time.perf_counter() - t
-        if ws > 1:
-            tt = torch.tensor([el], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(time.perf_counter() - t, ws, dev)
         e2e_same = bool(np.array_equal(r.numpy(), res))
         # pinned inputs are read in place over NVLink-C2C: every y once (8 B/point) and
         # x at about 7 x 32 probes per bin edge plus the preselected points
         h2d = 8 * n + 8 * (N_OUT * R_PS // 2 + 1) * 7 * 32 + 16 * (N_OUT * R_PS + 2)
-        e2e = {"value": ws * n * E / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_rate(n * E, ws, el), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8 * N_OUT + 8, "steps": E, "matches_device_result": e2e_same,
                "mode": "zero-copy: pinned host x/y read in place by the kernels over NVLink-C2C"}
         del dbuf
@@ -335,7 +344,7 @@ def main():
                "sample": f"the full workload once ({n} points), single-threaded C oracle"}
         parity = "bit-exact" if np.array_equal(ref, res) else "MISMATCH"
 
-    value = ws * n / (ms * 1e-3) / 1e9
+    value = job_rate(n, ws, ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
