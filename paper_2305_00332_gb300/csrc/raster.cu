@@ -4,16 +4,19 @@
 //
 //  k_raster         a warp per segment, or per 31 consecutive segments when there are
 //                   many.  Lanes map the points to canvas coordinates (FP64, then
-//                   float32), once per point; per segment the warp reads the masks
-//                   of the segment's pixel box 32 at a time and tests the pixels that
-//                   are not fully inked yet, two per step: each half-warp tests the
-//                   16 samples of one pixel (one sample per lane, float32 with every
-//                   operation rounded on its own), and one ballot yields both pixels'
-//                   sample masks, OR-ed into the canvas with a reduction.
+//                   float32), once per point.  When the union of the group's pixel
+//                   boxes is small (dense charts) its masks are read once and each
+//                   segment tests only the open pixels of its box; otherwise each box
+//                   is read 32 masks at a time.  Pixels are tested two per step: each
+//                   half-warp tests the 16 samples of one pixel (one sample per lane,
+//                   float32 with every operation rounded on its own), and one ballot
+//                   yields both pixels' sample masks, OR-ed into the canvas.
 //  k_intensity      16ths of ink -> 8-bit intensity, one thread per pixel.
 //  k_visual_counts  per pixel |ref - img| > margin, (ref - img)^2 and whether the
 //                   3 x 3 neighbourhood of the reference holds ink; block sums, one
 //                   64-bit atomic add per block and count (integers: exact, order-free).
+#include <limits.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -90,7 +93,56 @@ __device__ __forceinline__ int floor_clamped(float v, int lim) {
   return (int)floorf(fminf(fmaxf(v, -4.0f), (float)lim + 4.0f));
 }
 
+// The pixel box of segment A-B (R: [floor(min) - 1, floor(max) + 1] on both axes),
+// clipped to the canvas; false when it is empty or an endpoint is NaN (such a segment
+// inks nothing).
+__device__ __forceinline__ bool segment_box(const RasterArgs& a, float ax, float ay, float bx, float by, int* c0,
+                                            int* c1, int* r0, int* r1) {
+  if (isnan(ax) || isnan(ay) || isnan(bx) || isnan(by)) return false;
+  const float lox = ax < bx ? ax : bx, hix = ax < bx ? bx : ax;
+  const float loy = ay < by ? ay : by, hiy = ay < by ? by : ay;
+  *c0 = max(floor_clamped(lox, a.W) - 1, 0);
+  *c1 = min(floor_clamped(hix, a.W) + 1, a.W - 1);
+  *r0 = max(floor_clamped(loy, a.H) - 1, 0);
+  *r1 = min(floor_clamped(hiy, a.H) + 1, a.H - 1);
+  return *c0 <= *c1 && *r0 <= *r1;
+}
+
+// Test and ink the pixels of `todo` against segment A + t*(dx, dy): bit p is pixel p
+// of a listing whose (row << 16 | column) offsets from (r0, c0) lane p holds in rcA
+// (p < 32) or lane p - 32 in rcB.  Two pixels per step, one per half-warp, one sample
+// per lane; one ballot gives both pixels' masks, OR-ed into the canvas.
+__device__ __forceinline__ void ink_pixels(const RasterArgs& a, unsigned long long todo, unsigned rcA,
+                                           unsigned rcB, int r0, int c0, float ax, float ay, float dx, float dy,
+                                           float len2, int half, int s, float offx, float offy) {
+  while (todo) {
+    const int first = __ffsll(todo) - 1;
+    todo &= todo - 1;
+    const int second = todo ? __ffsll(todo) - 1 : -1;
+    if (todo) todo &= todo - 1;
+    const int mine = half ? second : first;
+    const int src = mine < 0 ? 0 : (mine & 31);
+    const unsigned pa = __shfl_sync(kFull, rcA, src), pb = __shfl_sync(kFull, rcB, src);
+    const unsigned prc = mine >= 32 ? pb : pa;
+    const int pr = r0 + (int)(prc >> 16), pc = c0 + (int)(prc & 0xffffu);
+    bool ink = false;
+    if (mine >= 0) ink = sample_inked(__fadd_rn((float)pc, offx), __fadd_rn((float)pr, offy), ax, ay, dx, dy, len2);
+    const unsigned b = __ballot_sync(kFull, ink);
+    if (s == 0 && mine >= 0) {
+      const unsigned m = half ? b >> 16 : b & 0xffffu;
+      if (m) atomicOr(a.mask + (int64_t)pr * a.W + pc, m);
+    }
+  }
+}
+
+// Whether the canvas pixel (r, c) is not fully inked yet.  Masks only grow, so a stale
+// read only costs a test that was not needed.
+__device__ __forceinline__ bool pixel_open(const RasterArgs& a, int r, int c) {
+  return (__ldcg(a.mask + (int64_t)r * a.W + c) & 0xffffu) != 0xffffu;
+}
+
 constexpr int kRasterThreads = 256;
+constexpr int kUnionPixels = 64;  // the union box of a warp's segments is read at once up to this size
 
 __global__ void __launch_bounds__(kRasterThreads) k_raster(const __grid_constant__ RasterArgs a) {
   const int lane = threadIdx.x & 31;
@@ -103,53 +155,72 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const __grid_constant
   const int G = a.group;
   for (int64_t base = (((int64_t)blockIdx.x * kRasterThreads + threadIdx.x) >> 5) * G; base < a.segments;
        base += warps * G) {
-    // lanes 0..G map the group's G + 1 points, once each (the FP64 pipe is narrow)
+    // lanes 0..G map the group's G + 1 points, once each (the FP64 pipe is narrow);
+    // lane j < gn holds segment j (its point and the next lane's)
     float cx = 0.0f, cy = 0.0f;
     if (lane <= G && base + lane <= a.segments) canvas_point(a, base + lane, sx, sy, zx, zy, &cx, &cy);
     const int gn = (int)min((int64_t)G, a.segments - base);
-    for (int j = 0; j < gn; ++j) {
+    const float nx = __shfl_down_sync(kFull, cx, 1), ny = __shfl_down_sync(kFull, cy, 1);
+    int sc0 = 0, sc1 = -1, sr0 = 0, sr1 = -1;
+    const bool sv = lane < gn && segment_box(a, cx, cy, nx, ny, &sc0, &sc1, &sr0, &sr1);
+    const unsigned live = __ballot_sync(kFull, sv);
+    if (!live) continue;
+    // the union of the segments' boxes
+    const int uc0 = __reduce_min_sync(kFull, sv ? sc0 : INT_MAX), uc1 = __reduce_max_sync(kFull, sv ? sc1 : -1);
+    const int ur0 = __reduce_min_sync(kFull, sv ? sr0 : INT_MAX), ur1 = __reduce_max_sync(kFull, sv ? sr1 : -1);
+    const int uw = uc1 - uc0 + 1, uh = ur1 - ur0 + 1;
+    if (uw <= kUnionPixels && uh <= kUnionPixels && uw * uh <= kUnionPixels) {
+      // Small union (dense charts): read its masks once; a segment only tests the open
+      // pixels of its own box, and a group whose union is fully inked costs one read.
+      const int unp = uw * uh;
+      const int pA = lane, pB = lane + 32;
+      const int rowA = pA / uw, colA = pA - rowA * uw, rowB = pB / uw, colB = pB - rowB * uw;
+      const unsigned rcA = ((unsigned)rowA << 16) | (unsigned)colA, rcB = ((unsigned)rowB << 16) | (unsigned)colB;
+      const bool okA = pA < unp, okB = pB < unp;
+      const bool openA = okA && pixel_open(a, ur0 + rowA, uc0 + colA);
+      const bool openB = okB && pixel_open(a, ur0 + rowB, uc0 + colB);
+      const unsigned long long open =
+          (unsigned long long)__ballot_sync(kFull, openA) | ((unsigned long long)__ballot_sync(kFull, openB) << 32);
+      if (!open) continue;
+      for (unsigned segs = live; segs; segs &= segs - 1) {
+        const int j = __ffs(segs) - 1;
+        const int c0 = __shfl_sync(kFull, sc0, j), c1 = __shfl_sync(kFull, sc1, j);
+        const int r0 = __shfl_sync(kFull, sr0, j), r1 = __shfl_sync(kFull, sr1, j);
+        const bool inA = okA && uc0 + colA >= c0 && uc0 + colA <= c1 && ur0 + rowA >= r0 && ur0 + rowA <= r1;
+        const bool inB = okB && uc0 + colB >= c0 && uc0 + colB <= c1 && ur0 + rowB >= r0 && ur0 + rowB <= r1;
+        const unsigned long long todo =
+            open & ((unsigned long long)__ballot_sync(kFull, inA) | ((unsigned long long)__ballot_sync(kFull, inB) << 32));
+        if (!todo) continue;
+        const float ax = __shfl_sync(kFull, cx, j), ay = __shfl_sync(kFull, cy, j);
+        const float bx = __shfl_sync(kFull, nx, j), by = __shfl_sync(kFull, ny, j);
+        const float dx = __fsub_rn(bx, ax), dy = __fsub_rn(by, ay);
+        const float len2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        ink_pixels(a, todo, rcA, rcB, ur0, uc0, ax, ay, dx, dy, len2, half, s, offx, offy);
+      }
+      continue;
+    }
+    // Large union: segment by segment, each box in chunks of 32 pixels whose open
+    // pixels are tested.
+    for (unsigned segs = live; segs; segs &= segs - 1) {
+      const int j = __ffs(segs) - 1;
+      const int c0 = __shfl_sync(kFull, sc0, j), c1 = __shfl_sync(kFull, sc1, j);
+      const int r0 = __shfl_sync(kFull, sr0, j), r1 = __shfl_sync(kFull, sr1, j);
       const float ax = __shfl_sync(kFull, cx, j), ay = __shfl_sync(kFull, cy, j);
-      const float bx = __shfl_sync(kFull, cx, j + 1), by = __shfl_sync(kFull, cy, j + 1);
-      if (isnan(ax) || isnan(ay) || isnan(bx) || isnan(by)) continue;  // inks nothing
-      const float lox = ax < bx ? ax : bx, hix = ax < bx ? bx : ax;
-      const float loy = ay < by ? ay : by, hiy = ay < by ? by : ay;
-      const int c0 = max(floor_clamped(lox, a.W) - 1, 0), c1 = min(floor_clamped(hix, a.W) + 1, a.W - 1);
-      const int r0 = max(floor_clamped(loy, a.H) - 1, 0), r1 = min(floor_clamped(hiy, a.H) + 1, a.H - 1);
-      if (c0 > c1 || r0 > r1) continue;
-      const int w = c1 - c0 + 1;
-      const int npix = w * (r1 - r0 + 1);
+      const float bx = __shfl_sync(kFull, nx, j), by = __shfl_sync(kFull, ny, j);
       const float dx = __fsub_rn(bx, ax), dy = __fsub_rn(by, ay);
       const float len2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-      // The box in chunks of 32 pixels: each lane reads one pixel's mask, and only
-      // pixels not yet fully inked are tested (masks only grow, so a stale read just
-      // tests a pixel that needed no test).  Two pixels per step, one per half-warp.
+      const int w = c1 - c0 + 1;
+      const int npix = w * (r1 - r0 + 1);
       for (int q0 = 0; q0 < npix; q0 += 32) {
         const int p = q0 + lane;
         unsigned rc = 0;  // (row << 16) | column within the box
-        bool need = false;
+        bool open = false;
         if (p < npix) {
           const int pr = p / w, pc = p - pr * w;
           rc = ((unsigned)pr << 16) | (unsigned)pc;
-          need = (__ldcg(a.mask + (int64_t)(r0 + pr) * a.W + (c0 + pc)) & 0xffffu) != 0xffffu;
+          open = pixel_open(a, r0 + pr, c0 + pc);
         }
-        unsigned todo = __ballot_sync(kFull, need);
-        while (todo) {
-          const int first = __ffs(todo) - 1;
-          todo &= todo - 1;
-          const int second = todo ? __ffs(todo) - 1 : -1;
-          if (todo) todo &= todo - 1;
-          const int mine = half ? second : first;
-          const unsigned prc = __shfl_sync(kFull, rc, mine < 0 ? 0 : mine);
-          const int pr = r0 + (int)(prc >> 16), pc = c0 + (int)(prc & 0xffffu);
-          bool ink = false;
-          if (mine >= 0)
-            ink = sample_inked(__fadd_rn((float)pc, offx), __fadd_rn((float)pr, offy), ax, ay, dx, dy, len2);
-          const unsigned b = __ballot_sync(kFull, ink);
-          if (s == 0 && mine >= 0) {
-            const unsigned m = half ? b >> 16 : b & 0xffffu;
-            if (m) atomicOr(a.mask + (int64_t)pr * a.W + pc, m);
-          }
-        }
+        ink_pixels(a, __ballot_sync(kFull, open), rc, 0u, r0, c0, ax, ay, dx, dy, len2, half, s, offx, offy);
       }
     }
   }
