@@ -1,10 +1,14 @@
 // C ABI of libmmlttb: argument checks, planning, workspace layout and the launch
 // sequence of the MinMaxLTTB hot path (arXiv 2305.00332, Sec. 3).
 //
-// Launch sequence for one series (all on the caller's stream, no host sync):
-//   memset(header) -> [k_edges] -> k_stream -> k_merge -> k_tables -> k_chain
-// (or k_lttb_grid instead of the table pair when LTTB buckets are large), or
-// k_iota when every index is kept.
+// Launch sequences for one series (all on the caller's stream, no host sync), by
+// launch path (single_path):
+//   split:       memset(header) -> [k_edges] -> k_stream -> k_bins -> k_binscan ->
+//                k_place -> k_tables -> k_chain (k_lttb_grid / k_lttb_block instead of
+//                the table pair when LTTB buckets are large)
+//   fused tail:  [k_edges] -> k_stream -> k_fused<0> (compaction and LTTB, one launch)
+//   fused:       memset(header) -> k_fused<1> (the whole call in one persistent launch)
+// or k_iota when every index is kept.
 #include <stdio.h>
 #include <string.h>
 
