@@ -308,7 +308,7 @@ def main():
     # end to end through the host-buffer C entry point: H2D of x and y, D2H of indices
     e2e = None
     if not args.no_e2e:
-        dbuf = torch.empty(mm.host_buffer_bytes(mm.F64, mm.X_I64, n, N_OUT, R_PS, mm.BINS_XWIDTH),
+        dbuf = torch.empty(mm.host_buffer_bytes(mm.F64, mm.X_I64, n, N_OUT, R_PS, mm.BINS_XWIDTH, inplace=True),
                            dtype=torch.uint8, device=dev)
         del y, x
         torch.cuda.empty_cache()

@@ -188,14 +188,19 @@ int mmlttb_minmaxlttb_noalloc(const void *y, int ydtype, const void *x, int xkin
  * series larger than device memory.  Pageable host memory is first copied into
  * `device_buffer`.  The indices and the count are copied back to out_host /
  * out_count_host and `stream` is synchronized before returning.
- *   device_buffer  device memory of at least mmlttb_host_buffer_bytes(...) bytes,
- *                  owned by the caller (holds the staged input, the output and the
- *                  workspace).
+ *   device_buffer  device memory owned by the caller, holding the output, the
+ *                  workspace and, for pageable inputs, the staged series: at least
+ *                  mmlttb_host_buffer_bytes(...) bytes, or, when y (and x) are
+ *                  pinned or registered, mmlttb_host_buffer_bytes_inplace(...) bytes,
+ *                  which do not grow with the series beyond its workspace (records
+ *                  per bin and warp, LTTB tables).  A smaller buffer: MMLTTB_ENOSPC.
  *   out_host       host int64[out_cap], out_cap >= min(n_out, n_in).
  *   out_count_host host int64 (nullable).
  */
 int mmlttb_host_buffer_bytes(int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
                              int binmode, size_t *bytes);
+int mmlttb_host_buffer_bytes_inplace(int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                                     int binmode, size_t *bytes);
 int mmlttb_minmaxlttb_host(const void *y_host, int ydtype, const void *x_host, int xkind,
                            int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
                            int64_t *out_host, int64_t out_cap, int64_t *out_count_host,

@@ -53,6 +53,8 @@ lib.mmlttb_workspace_status.restype = _int
 lib.mmlttb_workspace_status.argtypes = [_vp, ctypes.POINTER(_int), _vp]
 lib.mmlttb_host_buffer_bytes.restype = _int
 lib.mmlttb_host_buffer_bytes.argtypes = [_int, _int, _i64, _i64, _i32, _int, ctypes.POINTER(_sz)]
+lib.mmlttb_host_buffer_bytes_inplace.restype = _int
+lib.mmlttb_host_buffer_bytes_inplace.argtypes = [_int, _int, _i64, _i64, _i32, _int, ctypes.POINTER(_sz)]
 lib.mmlttb_minmaxlttb_host.restype = _int
 lib.mmlttb_minmaxlttb_host.argtypes = [_vp, _int, _vp, _int, _i64, _i64, _i32, _int, _vp, _i64, _vp,
                                        _vp, _sz, _vp]
@@ -233,18 +235,21 @@ def workspace_status(workspace):
     return st.value
 
 
-def host_buffer_bytes(ydtype, xkind, n_in, n_out, r_ps=4, binmode=BINS_INDEX):
-    """Device bytes mmlttb_minmaxlttb_host needs (staged input, output, workspace)."""
+def host_buffer_bytes(ydtype, xkind, n_in, n_out, r_ps=4, binmode=BINS_INDEX, inplace=False):
+    """Device bytes mmlttb_minmaxlttb_host needs: output, workspace and a staged copy
+    of the series (any host memory), or with inplace=True without the copy (pinned or
+    registered inputs, read in place)."""
     b = ctypes.c_size_t(0)
-    _check(lib.mmlttb_host_buffer_bytes(ydtype, xkind, n_in, n_out, r_ps, _binmode(binmode),
-                                        ctypes.byref(b)), "mmlttb_host_buffer_bytes")
+    f = lib.mmlttb_host_buffer_bytes_inplace if inplace else lib.mmlttb_host_buffer_bytes
+    _check(f(ydtype, xkind, n_in, n_out, r_ps, _binmode(binmode), ctypes.byref(b)), "mmlttb_host_buffer_bytes")
     return b.value
 
 
 def minmaxlttb_host(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, device_buffer=None,
                     device=None):
-    """MinMaxLTTB on host tensors (mmlttb_minmaxlttb_host): copies in, runs, copies the
-    indices back; blocking.  Pinned host tensors make the copies asynchronous DMA."""
+    """MinMaxLTTB on host tensors (mmlttb_minmaxlttb_host), blocking.  Pinned tensors
+    are read in place by the kernels (the device buffer then holds no copy of the
+    series, so the series may exceed device memory); pageable ones are staged."""
     _check_inputs(y, x)
     if y.is_cuda:
         raise ValueError("minmaxlttb_host takes host tensors")
@@ -255,7 +260,8 @@ def minmaxlttb_host(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, devi
     if out is None:
         out = torch.empty(cap, dtype=torch.int64)
     count = torch.zeros(1, dtype=torch.int64)
-    need = host_buffer_bytes(yd, xk, n, n_out, r_ps, bm)
+    inplace = y.is_pinned() and (x is None or x.is_pinned())
+    need = host_buffer_bytes(yd, xk, n, n_out, r_ps, bm, inplace=inplace)
     if device_buffer is None:
         device_buffer = torch.empty(need, dtype=torch.uint8, device=device)
     _check(lib.mmlttb_minmaxlttb_host(

@@ -435,9 +435,11 @@ const void* host_device_view(const void* p) {
   return nullptr;
 }
 
-// Device staging layout of mmlttb_minmaxlttb_host: y | x | out | count | workspace.
+// Device layout of mmlttb_minmaxlttb_host: out | count | workspace | y | x.  Inputs
+// read in place need only the part before y (inplace_total); pageable inputs are
+// staged in y | x (total).
 struct HostLayout {
-  size_t y = 0, x = 0, out = 0, count = 0, ws = 0, ws_bytes = 0, total = 0;
+  size_t y = 0, x = 0, out = 0, count = 0, ws = 0, ws_bytes = 0, inplace_total = 0, total = 0;
 };
 
 int host_layout(int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int binmode,
@@ -456,10 +458,6 @@ int host_layout(int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int bin
   const int64_t cap = n_out < n ? n_out : n;
   HostLayout l;
   size_t off = 0;
-  l.y = off;
-  off = align256(off + (size_t)n * es);
-  l.x = off;
-  off = align256(off + (xk == MMLTTB_X_IMPLICIT ? 0 : (size_t)n * 8));
   l.out = off;
   off = align256(off + (size_t)(cap > 0 ? cap : 1) * 8);
   l.count = off;
@@ -467,6 +465,11 @@ int host_layout(int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps, int bin
   l.ws = off;
   l.ws_bytes = p.total;
   off = align256(off + p.total);
+  l.inplace_total = off;
+  l.y = off;
+  off = align256(off + (size_t)n * es);
+  l.x = off;
+  off = align256(off + (xk == MMLTTB_X_IMPLICIT ? 0 : (size_t)n * 8));
   l.total = off;
   *L = l;
   return MMLTTB_OK;
@@ -556,6 +559,16 @@ int mmlttb_host_buffer_bytes(int ydtype, int xkind, int64_t n_in, int64_t n_out,
   return MMLTTB_OK;
 }
 
+int mmlttb_host_buffer_bytes_inplace(int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps,
+                                     int binmode, size_t* bytes) {
+  if (!bytes) return MMLTTB_EINVAL;
+  HostLayout l;
+  int rc = host_layout(ydtype, xkind, n_in, n_out, r_ps, binmode, &l);
+  if (rc) return rc;
+  *bytes = l.inplace_total;
+  return MMLTTB_OK;
+}
+
 int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, int xkind,
                            int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
                            int64_t* out_host, int64_t out_cap, int64_t* out_count_host,
@@ -568,17 +581,19 @@ int mmlttb_minmaxlttb_host(const void* y_host, int ydtype, const void* x_host, i
   const int64_t need = n_out < n_in ? n_out : n_in;
   if (need > 0 && out_host == nullptr) return MMLTTB_EINVAL;
   if (out_cap < need) return MMLTTB_ERANGE;
-  if (device_buffer == nullptr || device_bytes < l.total) return MMLTTB_ENOSPC;
   cudaStream_t st = (cudaStream_t)stream;
   char* b = (char*)device_buffer;
   const size_t es = ydtype == MMLTTB_F32 ? 4 : 8;
   cudaError_t e;
   // Pinned or registered host memory is read in place by the kernels (over the
   // CPU-GPU link): only the bytes the path touches cross it, i.e. every y once and x
-  // only at bin-edge probes and preselected points.  Pageable memory is staged.
+  // only at bin-edge probes and preselected points, and the device buffer holds no
+  // copy of the series.  Pageable memory is staged.
   const void* yd = host_device_view(y_host);
   const void* xd = xkind == MMLTTB_X_IMPLICIT ? nullptr : host_device_view(x_host);
-  if (n_in > 0 && (!yd || (xkind != MMLTTB_X_IMPLICIT && !xd))) {
+  const bool staged = n_in > 0 && (!yd || (xkind != MMLTTB_X_IMPLICIT && !xd));
+  if (device_buffer == nullptr || device_bytes < (staged ? l.total : l.inplace_total)) return MMLTTB_ENOSPC;
+  if (staged) {
     if ((e = cudaMemcpyAsync(b + l.y, y_host, (size_t)n_in * es, cudaMemcpyHostToDevice, st)))
       return cuda_fail(e);
     yd = b + l.y;

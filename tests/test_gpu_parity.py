@@ -256,6 +256,26 @@ def test_host_entry_point(mm, ref, pinned):
         eq(dev_res, exp, "device entry")
 
 
+def test_host_series_need_no_device_copy(mm, ref):
+    """Pinned inputs run with the in-place device buffer, which holds no copy of the
+    series (so a series may exceed device memory); pageable inputs need the staging
+    size and get MMLTTB_ENOSPC (-2) with the smaller buffer."""
+    n = 20_000_003
+    y = synth.random_walk(n, seed=22, dtype=np.float64)
+    x = synth.exp_gaps_x(n, seed=22, mean_gap=10.0, big_gaps=2, big_gap=10**7)
+    yh, xh = torch.from_numpy(y).pin_memory(), torch.from_numpy(x).pin_memory()
+    small = mm.host_buffer_bytes(mm.F64, mm.X_I64, n, 4000, 4, mm.BINS_XWIDTH, inplace=True)
+    full = mm.host_buffer_bytes(mm.F64, mm.X_I64, n, 4000, 4, mm.BINS_XWIDTH)
+    assert small < n * 8 // 4 and full >= small + 16 * n
+    buf = torch.empty(small, dtype=torch.uint8, device="cuda")
+    got = mm.minmaxlttb_host(yh, 4000, 4, x=xh, binmode="xwidth", device_buffer=buf).numpy()
+    eq(got, ref.minmaxlttb(y, 4000, 4, x=x, binmode="xwidth"), "in place")
+    with pytest.raises(mm.MMLTTBError) as e:
+        mm.minmaxlttb_host(torch.from_numpy(y), 4000, 4, x=torch.from_numpy(x), binmode="xwidth",
+                           device_buffer=buf)
+    assert e.value.code == -2
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 7, 100, 4097, 100_003])
 @pytest.mark.parametrize("kind", ["walk32", "walk64", "ties32", "zeros64", "const32"])
 def test_m4_index_bins(mm, ref, n, kind):
