@@ -441,13 +441,13 @@ inline cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
 cudaError_t launch_edges(const Batch& bt, cudaStream_t st);
 // Stream-kernel variants (see stream_variant_info); launch_stream runs one of them.
 constexpr int kStreamVariants = 3;
-// ymode: 0 any y (dispatch per series), 1 float32 only, 2 float64 only (no NaN-aware
-// series); see stream_ymode.
+// ymode: 0 any y (dispatch per series), 1 float32 only, 2 float64 only, 3 float32
+// NaN-aware only, 4 float64 NaN-aware only; see stream_ymode.
 cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode, cudaStream_t st);
 // The stream-kernel y mode for series of y type ydt: the specialised kernel unless the
 // NaN-aware rule applies.
 inline int stream_ymode(int ydt, bool nan_aware) {
-  if (nan_aware) return 0;
+  if (nan_aware) return ydt == MMLTTB_F32 ? 3 : 4;
   return ydt == MMLTTB_F32 ? 1 : 2;
 }
 int stream_variant_info(int variant, int* unroll, int* min_blocks);

@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
 
 }  // namespace
 
-// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6), each for any y, float32
-// and float64 y.
+// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6), each for any y and for
+// float32 and float64 y with and without the NaN-aware rule.
 template <int kY>
 static const void* stream_kernel_y(int v) {
   switch (v) {
@@ -46,6 +46,8 @@ static const void* stream_kernel(int v, int ymode) {
   switch (ymode) {
     case kYF32: return stream_kernel_y<kYF32>(v);
     case kYF64: return stream_kernel_y<kYF64>(v);
+    case kYF32Nan: return stream_kernel_y<kYF32Nan>(v);
+    case kYF64Nan: return stream_kernel_y<kYF64Nan>(v);
     default: return stream_kernel_y<kYAny>(v);
   }
 }
@@ -61,7 +63,7 @@ int stream_variant_info(int v, int* unroll, int* min_blocks) {
 int stream_blocks_per_sm(int v) {
   int bps = 0;
   int b0 = 0;
-  for (int y = kYAny; y <= kYF64; ++y) {  // the smallest occupancy of the variant's kernels
+  for (int y = kYAny; y <= kYF64Nan; ++y) {  // the smallest occupancy of the variant's kernels
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v, y), kStreamThreads, 0) !=
         cudaSuccess)
       return 1;
@@ -92,6 +94,8 @@ cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode,
   switch (ymode) {
     case kYF32: return launch_stream_y<kYF32>(bt, g, b, variant, st);
     case kYF64: return launch_stream_y<kYF64>(bt, g, b, variant, st);
+    case kYF32Nan: return launch_stream_y<kYF32Nan>(bt, g, b, variant, st);
+    case kYF64Nan: return launch_stream_y<kYF64Nan>(bt, g, b, variant, st);
     default: return launch_stream_y<kYAny>(bt, g, b, variant, st);
   }
 }

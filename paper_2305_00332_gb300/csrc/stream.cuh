@@ -343,9 +343,10 @@ __device__ __forceinline__ int64_t point_at_work(int64_t t, int64_t N, const Div
 }
 
 // y kinds a stream kernel is compiled for: any (dispatch on the plan's type and
-// NaN-aware flag) or one type without the NaN-aware rule.  A kernel specialised to one
-// kind inlines one segment routine instead of four and keeps its state in registers.
-enum YMode : int { kYAny = 0, kYF32 = 1, kYF64 = 2 };
+// NaN-aware flag), or one type with or without the NaN-aware rule.  A kernel
+// specialised to one kind inlines one segment routine instead of calling one of four
+// and keeps its state in registers.
+enum YMode : int { kYAny = 0, kYF32 = 1, kYF64 = 2, kYF32Nan = 3, kYF64Nan = 4 };
 
 // One warp over the binned points [p_lo, p_hi) of one series.  The warp splits into
 // 32/G groups of G lanes (G chosen per series from its mean bin size) and each group
@@ -389,6 +390,10 @@ __device__ void warp_series_range(const Batch& bt, const SeriesPlan& sp, int64_t
         r = segment_f32<kUnroll, false>((const float*)sp.y, lo, hi, gl, G);
       } else if constexpr (kY == kYF64) {
         r = segment_f64<kUnroll, false>((const double*)sp.y, lo, hi, gl, G);
+      } else if constexpr (kY == kYF32Nan) {
+        r = segment_f32<kUnroll, true>((const float*)sp.y, lo, hi, gl, G);
+      } else if constexpr (kY == kYF64Nan) {
+        r = segment_f64<kUnroll, true>((const double*)sp.y, lo, hi, gl, G);
       } else {
         r = segment_any<kUnroll>(sp, lo, hi, gl, G);
       }
