@@ -111,12 +111,20 @@ __global__ void __launch_bounds__(kGridThreads) k_lttb_grid(const __grid_constan
   if (m <= sp.n_out) return;  // k_chain copied the points
   const int64_t K = sp.n_out - 2, N = m - 2;
   const int64_t G = gridDim.x, c = blockIdx.x;
-  // Phase A: every next-bucket mean, one thread per bucket, dealt round-robin over the
-  // CTAs: each mean is a long dependent FP64 sum, and the FP64 pipe is narrow.
-  for (int64_t j = (int64_t)threadIdx.x * G + c; j < K; j += G * blockDim.x) {
+  // Phase A: every next-bucket mean, one warp per bucket, dealt round-robin over the
+  // CTAs (bucket_mean_warp: lane-parallel when the sums are exact in any order, else
+  // the sequential sums of one lane).
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t j = (int64_t)(threadIdx.x >> 5) * G + c; j < K; j += G * wpb) {
     int64_t lo, hi;
     next_bucket(j, sp.dK, N, m, &lo, &hi);
-    bucket_mean(sp, lo, hi, &sp.means[2 * j], &sp.means[2 * j + 1]);
+    double xc, yc;
+    bucket_mean_warp(sp, lo, hi, lane, &xc, &yc);
+    if (lane == 0) {
+      sp.means[2 * j] = xc;
+      sp.means[2 * j + 1] = yc;
+    }
   }
   if (!grid_barrier(bt.barrier, (unsigned)G, bt.status)) return;
   __shared__ long long s_pick;
@@ -169,10 +177,16 @@ __global__ void __launch_bounds__(kGridThreads) k_lttb_block(const __grid_consta
   const int64_t m = lttb_m(sp);
   if (m <= sp.n_out) return;
   const int64_t K = sp.n_out - 2, N = m - 2;
-  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t j = threadIdx.x >> 5; j < K; j += blockDim.x >> 5) {  // a warp per bucket mean
     int64_t lo, hi;
     next_bucket(j, sp.dK, N, m, &lo, &hi);
-    bucket_mean(sp, lo, hi, &sp.means[2 * j], &sp.means[2 * j + 1]);
+    double xc, yc;
+    bucket_mean_warp(sp, lo, hi, lane, &xc, &yc);
+    if (lane == 0) {
+      sp.means[2 * j] = xc;
+      sp.means[2 * j + 1] = yc;
+    }
   }
   __syncthreads();
   int64_t a = 0;

@@ -61,6 +61,80 @@ __device__ void bucket_mean(const SeriesPlan& sp, int64_t lo, int64_t hi, double
   *yc = __ddiv_rn(sy, cnt);
 }
 
+// Exponent bookkeeping for exact sums.  A finite double v != 0 is a multiple of
+// 2^g(v) (g = the weight of its lowest set significand bit) and below 2^(e(v)+1) in
+// magnitude (e = its unbiased exponent).  If every term of a sum is a multiple of 2^G
+// and n * 2^(E+1) <= 2^(53+G) (G, E the smallest g and largest e), every partial sum
+// in ANY order is a multiple of 2^G below 2^(53+G): representable, so no addition
+// rounds and all orders give the same, exact sum -- the left-to-right FP64 sum of R7.
+struct ExactSum {
+  int gmin = INT_MAX, emax = INT_MIN;
+  bool bad = false;  // inf or NaN seen
+  __device__ void add(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int be = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    if (be == 0x7ff) {
+      bad = true;
+    } else if (be != 0 || m != 0) {
+      const unsigned long long sig = be ? (m | (1ull << 52)) : m;  // value = sig * 2^(max(be,1) - 1075)
+      const int scale = (be ? be : 1) - 1075;
+      const int g = scale + __ffsll((long long)sig) - 1;
+      const int e = scale + 63 - __clzll((long long)sig);
+      gmin = g < gmin ? g : gmin;
+      emax = e > emax ? e : emax;
+    }
+  }
+  // warp-wide: whether a sum of n terms is exact in any order (every lane gets it)
+  __device__ bool exact(int64_t n) {
+    const int g = __reduce_min_sync(kFull, gmin), e = __reduce_max_sync(kFull, emax);
+    const bool anybad = __any_sync(kFull, bad);
+    if (anybad) return false;
+    if (g == INT_MAX) return true;  // all terms zero
+    const int lg = 64 - __clzll((long long)(n > 1 ? n - 1 : 1));  // ceil(log2 n)
+    return lg + e + 1 <= 53 + g;
+  }
+};
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, d));
+  return v;
+}
+
+// Mean of LTTB positions [lo, hi) formed by a whole warp (all lanes call it): when the
+// bucket's sums are exact in any order (ExactSum) the lanes add strided terms and the
+// warp combines them, which equals the left-to-right sums of R7 bit for bit; otherwise
+// lane 0 forms the sequential sums.  One IEEE division each.  Results in every lane.
+__device__ void bucket_mean_warp(const SeriesPlan& sp, int64_t lo, int64_t hi, int lane, double* xc, double* yc) {
+  const bool xclosed = sp.xk == MMLTTB_X_IMPLICIT && !sp.sel && hi > 0 && hi - lo <= ((1ll << 53) - 1) / hi;
+  double sx = 0.0, sy = 0.0;
+  ExactSum ex, ey;
+  for (int64_t p = lo + lane; p < hi; p += 32) {
+    double xp, yp;
+    pos_xy(sp, p, &xp, &yp);
+    if (!xclosed) {
+      ex.add(xp);
+      sx = __dadd_rn(sx, xp);
+    }
+    ey.add(yp);
+    sy = __dadd_rn(sy, yp);
+  }
+  const bool fast = (xclosed || ex.exact(hi - lo)) && ey.exact(hi - lo);
+  if (fast) {
+    sy = warp_sum_f64(sy);
+    sx = xclosed ? (double)((lo + hi - 1) * (hi - lo) / 2) : warp_sum_f64(sx);
+    const double cnt = (double)(hi - lo);
+    *xc = __ddiv_rn(sx, cnt);
+    *yc = __ddiv_rn(sy, cnt);
+    return;
+  }
+  double a = 0.0, b = 0.0;
+  if (lane == 0) bucket_mean(sp, lo, hi, &a, &b);
+  *xc = __shfl_sync(kFull, a, 0);
+  *yc = __shfl_sync(kFull, b, 0);
+}
+
 // Bounds of the bucket after bucket j (R1), or the last point for the last bucket (R5).
 __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N, int64_t m,
                                             int64_t* lo, int64_t* hi) {

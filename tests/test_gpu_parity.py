@@ -148,6 +148,27 @@ def test_misaligned_y(mm, ref, dtype, offset):
        ref.minmaxlttb(y, 400, 4, x=x, binmode="xwidth"), "misaligned xwidth")
 
 
+def test_large_bucket_means_exact_and_fallback(mm, ref):
+    """Next-bucket means of large buckets (grid engine; one CTA per series in a
+    batch): integer-valued y, whose sums are exact in any order (the lanes add in
+    parallel), y whose magnitudes span 2^-60..2^60 in every bucket (the sums round:
+    one lane adds left to right), float32 y, and signed zeros all equal the oracle."""
+    r = np.random.default_rng(12)
+    n = 200_003
+    yi = np.cumsum(r.integers(-3, 4, n)).astype(np.float64)
+    ys = r.standard_normal(n) * 2.0 ** r.integers(-60, 61, n)
+    yz = np.where(r.random(n) < 0.5, -0.0, 0.0)
+    yz[::1001] = 1.0
+    series = [("int", yi), ("span", ys), ("span32", ys.astype(np.float32)), ("zeros", yz)]
+    for name, y in series:
+        for n_out in (40, 300):
+            eq(mm.lttb(dev(y), n_out), ref.lttb(y, n_out), f"grid lttb {name} n_out={n_out}")
+    b = mm.Batch([{"y": dev(y), "n_out": 40, "op": "lttb"} for _, y in series])
+    b.run()
+    for (name, y), got in zip(series, b.results()):
+        eq(got, ref.lttb(y, 40), f"block lttb {name}")
+
+
 def test_table_engine_threshold(mm, ref):
     """Bucket sizes around the transition-table limit (32 points)."""
     y = make("walk64", 10_000, seed=5)
