@@ -384,6 +384,16 @@ def stream_source_hash():
     return h.hexdigest()[:16]
 
 
+def profile_summary(path):
+    """The `- key: value` lines of a committed ncu summary, as a dict of strings."""
+    kv = {}
+    for line in open(path):
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    return kv
+
+
 def profiled_traffic(n):
     """DRAM bytes per launch of the streaming kernel from the committed ncu summary,
     scaled to n points; None when the summary is absent or the kernel's sources
@@ -391,11 +401,7 @@ def profiled_traffic(n):
     path = os.path.join(ROOT, "profiles", "k_stream_xwidth_f64.md")
     if not os.path.exists(path):
         return None
-    kv = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            kv[k.strip()] = v.strip().strip("`")
+    kv = profile_summary(path)
     if kv.get("kernel sources sha256[:16]") != stream_source_hash():
         return None
     try:

@@ -55,3 +55,15 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.25, 1) == 3.25
     assert bench.job_rate(1e9, 1, 1.25) == 0.8
+
+
+def test_committed_stream_profile_is_readable():
+    """The ncu summary that bench.py reads for `traffic` parses: a 16-hex-digit hash
+    of the kernel sources and a DRAM bytes-per-point figure near the 8 bytes the
+    float64 stream must read."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kv = bench.profile_summary(os.path.join(ROOT, "profiles", "k_stream_xwidth_f64.md"))
+    h = kv["kernel sources sha256[:16]"]
+    assert len(h) == 16 and all(c in "0123456789abcdef" for c in h)
+    assert 8.0 <= float(kv["dram bytes per point"]) < 8.5
