@@ -375,12 +375,22 @@ def main():
 STREAM_SOURCES = ("minmax.cu", "stream.cuh", "common.cuh")
 
 
+def _code_only(text):
+    """C/C++ source without its comments and blank lines (comments do not change the
+    compiled kernel; these sources hold no comment markers inside string literals)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def stream_source_hash():
+    """sha256[:16] of the streaming kernel's sources, comments removed."""
     import hashlib
     h = hashlib.sha256()
-    for f in STREAM_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2305_00332_gb300", "csrc", f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "mmlttb.h"), "rb").read())
+    paths = [os.path.join(ROOT, "paper_2305_00332_gb300", "csrc", f) for f in STREAM_SOURCES]
+    for path in paths + [os.path.join(ROOT, "include", "mmlttb.h")]:
+        h.update(_code_only(open(path).read()).encode())
     return h.hexdigest()[:16]
 
 
