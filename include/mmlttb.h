@@ -79,6 +79,8 @@ extern "C" {
 /* Opaque CUDA stream handle; binary-compatible with cudaStream_t. */
 typedef struct CUstream_st *mmlttb_stream;
 
+/* Library infrastructure (no counterpart in the paper): return-code text, the last
+   CUDA error and the version. */
 /* Human-readable text for a return code; never NULL, static storage. */
 const char *mmlttb_strerror(int code);
 
@@ -89,7 +91,8 @@ int mmlttb_last_cuda_error(void);
 int mmlttb_version(void);
 
 /*
- * Workspace size (bytes, on the current device) needed by `op` for these sizes.
+ * Workspace size (bytes, on the current device) needed by `op` for these sizes (no
+ * counterpart in the paper: the caller-owned scratch of the operations below).
  * Writes the size to *bytes.  The size depends only on the arguments and on the
  * current device's SM count.  Returns MMLTTB_OK or MMLTTB_EINVAL.
  */
@@ -181,7 +184,8 @@ int mmlttb_minmaxlttb_noalloc(const void *y, int ydtype, const void *x, int xkin
                               int64_t out_cap, int64_t *out_count, mmlttb_stream stream);
 
 /*
- * MinMaxLTTB on HOST buffers, end to end (blocking).  Pinned or registered host
+ * MinMaxLTTB (Sec. 3) on HOST buffers, end to end (blocking): the setting of series
+ * of billions of points held outside the accelerator (Sec. 1).  Pinned or registered host
  * memory (cudaHostAlloc / cudaHostRegister) is read in place by the kernels over
  * the CPU-GPU link, so only what the path touches crosses it: every y value once,
  * x only at the bin-edge probes and the preselected points.  This also serves
@@ -207,8 +211,10 @@ int mmlttb_minmaxlttb_host(const void *y_host, int ydtype, const void *x_host, i
                            void *device_buffer, size_t device_bytes, mmlttb_stream stream);
 
 /*
- * Batches (many series in one launch sequence).  Each series is described by a
- * mmlttb_series_desc; its op selects MinMaxLTTB, plain LTTB or preselection only,
+ * Batches (many series in one launch sequence; the paper treats one series at a
+ * time, batching is this library's).  Each series is described by a
+ * mmlttb_series_desc; its op selects MinMaxLTTB (Sec. 3), plain LTTB (Sec. 2.2.1),
+ * M4 (Sec. 2.2.1, Table 1) or preselection only (Sec. 3),
  * with the same semantics and argument rules as the single-series entry points.
  * All series run in one sequence of kernels: one MinMax stream over the interior
  * points of every series (cut into equal slices, one per warp, whatever the series
@@ -316,6 +322,7 @@ int mmlttb_server_reset_stats(mmlttb_server_t server);
 int mmlttb_server_destroy(mmlttb_server_t server);
 
 /*
+ * Measurement support (no counterpart in the paper).
  * Profiling hook (per calling thread, one shot): the next call that runs MinMax
  * preselection records `start_event` on its stream just before the streaming
  * MinMax kernel and `stop_event` just after it, then forgets both.  The events
@@ -335,7 +342,8 @@ int mmlttb_set_timing_events(void *start_event, void *stop_event);
 int mmlttb_set_stage_events(void *const *events, int count);
 
 /*
- * Autotuning of the streaming MinMax kernel (the HBM-bound step).  The library
+ * Autotuning of the streaming MinMax kernel (the HBM-bound step of the MinMax
+ * preselection, Sec. 3; tuning has no counterpart in the paper).  The library
  * carries several compiled variants of it, differing in 16-byte loads in flight
  * per lane and in resident CTAs per SM (see mmlttb_stream_variant_info); the
  * number of lanes that share a bin is chosen per series from its mean bin size.

@@ -44,6 +44,8 @@ extern "C" {
 #define MMLTTB_RASTER_MAX_SIDE 65536
 
 /*
+ * The line chart of a (downsampled) series, as rendered for the visual comparison of
+ * Sec. 4 (linear interpolation, 2-pixel lines, anti-aliased; readings above).
  * Rasterise the polyline through points idx[0..k) of the series (x, y) -- or
  * through all n_in points when idx is NULL (k is then ignored) -- and OR each
  * pixel's 16-bit sample mask into mask[r * width + c] (device uint32[height *
@@ -67,6 +69,7 @@ int mmlttb_raster(const void *y, int ydtype, const void *x, int xkind, int64_t n
                   int32_t width, int32_t height, uint32_t *mask, mmlttb_stream stream);
 
 /*
+ * Anti-aliased intensity of a rendered chart (Sec. 4 renders; coverage reading above).
  * 8-bit intensities of a canvas of sample masks: out[p] = (popcount(mask[p] &
  * 0xffff) * 255 + 8) / 16 for p < pixels (device arrays).  MMLTTB_EINVAL for NULL
  * pointers or pixels < 0.
@@ -75,6 +78,8 @@ int mmlttb_raster_intensity(const uint32_t *mask, int64_t pixels, uint8_t *out,
                             mmlttb_stream stream);
 
 /*
+ * The visual metrics of Sec. 4 (PEM_20 and MSE over the conv-mask, as named in the
+ * caption of the visual-representativeness figure; DSSIM is not provided).
  * Exact integer counts behind PEM_margin and MSE for a reference image `ref` and an
  * image `img` (device uint8[height * width], row-major):
  *   counts[0] = pixels with |ref - img| > margin,
