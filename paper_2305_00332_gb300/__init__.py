@@ -421,6 +421,18 @@ def visual_metrics(ref, img, margin=20):
     return {"pem": over / size if size else 0.0, "mse": sq / size if size else 0.0, "mask": size}
 
 
+# ---- failure-detection diagnostics (include/mmlttb_diag.h) ----
+DIAG_FUSED_BARRIER, DIAG_GRID_BARRIER = 0, 1
+lib.mmlttb_diag_wait_timeout.argtypes = [_int, _vp, _sz, _vp]
+
+
+def diag_wait_timeout(which, workspace):
+    """Run a bounded barrier wait that nothing satisfies (mmlttb_diag_wait_timeout);
+    afterwards workspace_status(workspace) reports bit 1.  Asynchronous (about 2 s)."""
+    _check(lib.mmlttb_diag_wait_timeout(which, workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                        _stream(workspace.device)), "mmlttb_diag_wait_timeout")
+
+
 lib.mmlttb_set_single_path.argtypes = [_int]
 lib.mmlttb_single_path.argtypes = [_int, _int, _int, _i64, _i64, _i32, _int]
 

@@ -73,6 +73,13 @@ __device__ bool grid_sync(const Batch& bt) {
   return s_ok != 0;
 }
 
+// Failure-detection probe: a two-CTA launch in which CTA 1 never arrives, so CTA 0's
+// grid_sync wait runs out (kWaitNs), sets status bit 1 and the kernel returns.
+__global__ void k_sync_probe(const __grid_constant__ Batch bt) {
+  if (blockIdx.x == 1) return;
+  grid_sync(bt);
+}
+
 __device__ __forceinline__ long long warp_sum64(long long v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
@@ -335,6 +342,11 @@ cudaError_t launch_fused_t(const Batch& bt, int grid, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_sync_probe(const Batch& bt, cudaStream_t st) {
+  k_sync_probe<<<2, 32, 0, st>>>(bt);
+  return cudaGetLastError();
+}
 
 // CTAs of the fused kernel: one per SM when one 512-thread CTA with the largest
 // staged table fits on an SM, else 0 (the fused path is then not used).

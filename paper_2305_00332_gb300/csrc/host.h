@@ -33,6 +33,10 @@ int64_t stream_warp_cap(const DevInfo& d);
 // Streaming warps of `variant` for `work` units: every warp gets at least one point.
 int64_t stream_warps(const DevInfo& d, int variant, int64_t work);
 
+// Failure-detection probes (a bounded wait that nothing satisfies; see mmlttb_diag.h).
+cudaError_t launch_sync_probe(const Batch& bt, cudaStream_t st);     // fused.cu grid_sync
+cudaError_t launch_barrier_probe(const Batch& bt, cudaStream_t st);  // lttb.cu grid_barrier
+
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kHeader = 256;  // workspace header: status word @0, barrier counter @4, m @8
 

@@ -75,6 +75,13 @@ __device__ bool grid_barrier(unsigned* ctr, unsigned target, unsigned* status) {
   return ok != 0;
 }
 
+// Failure-detection probe: a two-CTA launch in which CTA 1 never arrives, so CTA 0's
+// grid_barrier wait runs out (2 s), sets status bit 1 and the kernel returns.
+__global__ void k_barrier_probe(unsigned* ctr, unsigned* status) {
+  if (blockIdx.x == 1) return;
+  grid_barrier(ctr, 2u, status);
+}
+
 // Block-wide argmax of (area bits, position): the largest area, lowest position.
 __device__ void block_argmax(long long& ab, long long& pos) {
   __shared__ long long s_ab[32], s_pos[32];
@@ -220,6 +227,11 @@ __global__ void k_iota(int64_t* out, int64_t n, int64_t* out_count) {
 }
 
 }  // namespace
+
+cudaError_t launch_barrier_probe(const Batch& bt, cudaStream_t st) {
+  k_barrier_probe<<<2, 32, 0, st>>>(bt.barrier, bt.status);
+  return cudaGetLastError();
+}
 
 int lttb_grid_blocks_per_sm() {
   int bps = 0;

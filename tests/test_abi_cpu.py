@@ -123,3 +123,11 @@ def test_visual_metric_validation(lib):
     assert g(None, 4, 1, None) == -1
     assert g(1, -1, 1, None) == -1
     assert g(1, 0, 1, None) == 0
+
+
+def test_diag_probe_validation(lib):
+    f = lib.mmlttb_diag_wait_timeout
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert f(7, 1, 256, None) == -1      # unknown barrier kind
+    assert f(0, None, 256, None) == -1   # NULL workspace
+    assert f(1, 1, 255, None) == -1      # smaller than the header
