@@ -1,6 +1,6 @@
 /*
- * mmlttb_diag.h -- failure-detection diagnostics of libmmlttb.so (no counterpart in
- * the paper).  The library's device-side waits (the grid barriers of the fused
+ * mmlttb_diag.h -- diagnostics of libmmlttb.so (no counterpart in the paper):
+ * failure detection and a precondition check.  The library's device-side waits (the grid barriers of the fused
  * single-series kernel and of the grid-wide LTTB engine) are bounded: a wait that is
  * not satisfied within 2 s sets bit 1 of the workspace status word
  * (mmlttb_workspace_status) and the kernel returns, leaving the context usable.
@@ -27,6 +27,22 @@ extern "C" {
  * `which`, a NULL workspace or fewer than 256 bytes.
  */
 int mmlttb_diag_wait_timeout(int which, void *workspace, size_t workspace_bytes, mmlttb_stream stream);
+
+/* Bits of mmlttb_check_series. */
+#define MMLTTB_CHECK_Y_NAN 0x1       /* y holds a NaN (MinMaxLTTB, LTTB and plain MinMax
+                                        then return unspecified indices) */
+#define MMLTTB_CHECK_X_DECREASES 0x2 /* x[i+1] < x[i] for some i (x must be non-decreasing) */
+#define MMLTTB_CHECK_X_NONFINITE 0x4 /* float64 x holds NaN or +-inf */
+
+/*
+ * Check the documented preconditions of a series (mmlttb.h) on the device: one
+ * read of y and x.  *flags (device uint32) is overwritten with the MMLTTB_CHECK_*
+ * bits of the violations found (0: none).  x is ignored for MMLTTB_X_IMPLICIT.
+ * MMLTTB_EINVAL for a NULL y (n_in > 0) or flags, a NULL x that is not implicit, bad
+ * enums or n_in < 0.
+ */
+int mmlttb_check_series(const void *y, int ydtype, const void *x, int xkind, int64_t n_in, uint32_t *flags,
+                        mmlttb_stream stream);
 
 #ifdef __cplusplus
 }

@@ -433,6 +433,23 @@ def diag_wait_timeout(which, workspace):
                                         _stream(workspace.device)), "mmlttb_diag_wait_timeout")
 
 
+CHECK_Y_NAN, CHECK_X_DECREASES, CHECK_X_NONFINITE = 0x1, 0x2, 0x4
+lib.mmlttb_check_series.argtypes = [_vp, _int, _vp, _int, _i64, _vp, _vp]
+
+
+def check_series(y, x=None):
+    """The documented preconditions of a series checked on the device
+    (mmlttb_check_series): a set of the violations found, of "y_nan",
+    "x_decreases" and "x_nonfinite" (empty when none)."""
+    _check_inputs(y, x)
+    flags = torch.zeros(1, dtype=torch.int32, device=y.device)
+    _check(lib.mmlttb_check_series(y.data_ptr(), _ydt(y), x.data_ptr() if x is not None else None, _xkind(x),
+                                   y.numel(), flags.data_ptr(), _stream(y.device)), "mmlttb_check_series")
+    f = int(flags.item())
+    return {name for bit, name in ((CHECK_Y_NAN, "y_nan"), (CHECK_X_DECREASES, "x_decreases"),
+                                   (CHECK_X_NONFINITE, "x_nonfinite")) if f & bit}
+
+
 lib.mmlttb_set_single_path.argtypes = [_int]
 lib.mmlttb_single_path.argtypes = [_int, _int, _int, _i64, _i64, _i32, _int]
 

@@ -131,3 +131,14 @@ def test_diag_probe_validation(lib):
     assert f(7, 1, 256, None) == -1      # unknown barrier kind
     assert f(0, None, 256, None) == -1   # NULL workspace
     assert f(1, 1, 255, None) == -1      # smaller than the header
+
+
+def test_check_series_validation(lib):
+    f = lib.mmlttb_check_series
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    assert f(None, 0, None, 0, 10, 1, None) == -1  # NULL y
+    assert f(1, 0, None, 0, 10, None, None) == -1  # NULL flags
+    assert f(1, 5, None, 0, 10, 1, None) == -1     # bad y type
+    assert f(1, 0, None, 1, 10, 1, None) == -1     # int64 x but NULL
+    assert f(1, 0, None, 0, -1, 1, None) == -1     # negative n
