@@ -121,14 +121,23 @@ def _binmode(binmode, nan_aware=False):
     raise ValueError(f"unknown bin mode {binmode!r}")
 
 
-def _check_inputs(y, x):
+def _check_inputs(y, x, cuda=True):
     if y.dim() != 1 or not y.is_contiguous():
         raise ValueError("y must be a contiguous 1-D tensor")
+    if cuda and not y.is_cuda:
+        raise ValueError("y must be a CUDA tensor (the kernels read device memory)")
     if x is not None:
         if x.dim() != 1 or not x.is_contiguous() or x.numel() != y.numel():
             raise ValueError("x must be a contiguous 1-D tensor of the same length as y")
         if x.device != y.device:
             raise ValueError("x and y must be on the same device")
+
+
+def _on(t, device, name):
+    """t must live on `device` (the kernels write or read it there)."""
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, not {t.device}")
+    return t
 
 
 def _stream(device):
@@ -146,7 +155,7 @@ def workspace_bytes(op, ydtype, xkind, n_in, n_out, r_ps=2, binmode=BINS_INDEX):
 def _workspace(nbytes, device, workspace):
     if workspace is None:
         return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
-    return workspace  # the C ABI checks the size (MMLTTB_ENOSPC)
+    return _on(workspace, device, "workspace")  # the C ABI checks the size (MMLTTB_ENOSPC)
 
 
 def _finish(out, count, sync):
@@ -165,6 +174,7 @@ def minmax_preselect(y, n_out, r_ps, x=None, binmode=BINS_INDEX, out=None, works
     cap = min(n, (n_out * r_ps // 2) * 2 + 2)
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    _on(out, y.device, "out")
     count = torch.empty(1, dtype=torch.int64, device=y.device)
     ws = _workspace(workspace_bytes(OP_PRESELECT, yd, xk, n, n_out, r_ps, bm), y.device, workspace)
     _check(lib.mmlttb_minmax_preselect(
@@ -183,6 +193,7 @@ def m4(y, n_out, x=None, binmode=BINS_INDEX, out=None, workspace=None, sync=True
     cap = min(n, 4 * (n_out // 4))
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    _on(out, y.device, "out")
     count = torch.empty(1, dtype=torch.int64, device=y.device)
     ws = _workspace(workspace_bytes(OP_M4, yd, xk, n, n_out, 4, bm), y.device, workspace)
     _check(lib.mmlttb_m4(
@@ -200,6 +211,7 @@ def lttb(y, n_out, x=None, out=None, workspace=None, sync=True):
     cap = min(n, n_out)
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    _on(out, y.device, "out")
     count = torch.empty(1, dtype=torch.int64, device=y.device)
     ws = _workspace(workspace_bytes(OP_LTTB, yd, xk, n, n_out), y.device, workspace)
     _check(lib.mmlttb_lttb(
@@ -218,6 +230,7 @@ def minmaxlttb(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, workspace
     cap = min(n, n_out)
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int64, device=y.device)
+    _on(out, y.device, "out")
     count = torch.empty(1, dtype=torch.int64, device=y.device)
     ws = _workspace(workspace_bytes(OP_MINMAXLTTB, yd, xk, n, n_out, r_ps, bm), y.device, workspace)
     _check(lib.mmlttb_minmaxlttb(
@@ -229,6 +242,8 @@ def minmaxlttb(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, workspace
 
 def workspace_status(workspace):
     """Status word of a workspace after the calls that used it (blocking)."""
+    if not workspace.is_cuda:
+        raise ValueError("workspace must be a CUDA tensor")
     st = ctypes.c_int(0)
     _check(lib.mmlttb_workspace_status(workspace.data_ptr(), ctypes.byref(st), _stream(workspace.device)),
            "mmlttb_workspace_status")
@@ -250,7 +265,7 @@ def minmaxlttb_host(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, devi
     """MinMaxLTTB on host tensors (mmlttb_minmaxlttb_host), blocking.  Pinned tensors
     are read in place by the kernels (the device buffer then holds no copy of the
     series, so the series may exceed device memory); pageable ones are staged."""
-    _check_inputs(y, x)
+    _check_inputs(y, x, cuda=False)
     if y.is_cuda:
         raise ValueError("minmaxlttb_host takes host tensors")
     device = torch.device(device if device is not None else "cuda")
@@ -264,6 +279,8 @@ def minmaxlttb_host(y, n_out, r_ps=4, x=None, binmode=BINS_INDEX, out=None, devi
     need = host_buffer_bytes(yd, xk, n, n_out, r_ps, bm, inplace=inplace)
     if device_buffer is None:
         device_buffer = torch.empty(need, dtype=torch.uint8, device=device)
+    if not device_buffer.is_cuda or out.is_cuda:
+        raise ValueError("device_buffer must be a CUDA tensor and out a host tensor")
     _check(lib.mmlttb_minmaxlttb_host(
         y.data_ptr(), yd, x.data_ptr() if x is not None else None, xk, n, n_out, r_ps, bm,
         out.data_ptr(), out.numel(), count.data_ptr(), device_buffer.data_ptr(),
@@ -375,6 +392,7 @@ def raster(y, extents, width, height, x=None, idx=None, mask=None):
         mask = torch.zeros((height, width), dtype=torch.int32, device=y.device)
     elif mask.dtype != torch.int32 or tuple(mask.shape) != (height, width) or not mask.is_contiguous():
         raise ValueError("mask must be a contiguous int32 tensor of shape (height, width)")
+    _on(mask, y.device, "mask")
     ip, k = None, 0
     if idx is not None:
         if idx.dtype != torch.int64 or idx.dim() != 1 or not idx.is_contiguous() or idx.device != y.device:
@@ -389,8 +407,8 @@ def raster(y, extents, width, height, x=None, idx=None, mask=None):
 
 def intensity(mask):
     """8-bit intensities of a canvas of sample masks (mmlttb_raster_intensity)."""
-    if mask.dtype != torch.int32 or not mask.is_contiguous():
-        raise ValueError("mask must be a contiguous int32 tensor")
+    if mask.dtype != torch.int32 or not mask.is_contiguous() or not mask.is_cuda:
+        raise ValueError("mask must be a contiguous int32 CUDA tensor")
     out = torch.empty(mask.shape, dtype=torch.uint8, device=mask.device)
     _check(lib.mmlttb_raster_intensity(mask.data_ptr(), mask.numel(), out.data_ptr(), _stream(mask.device)),
            "mmlttb_raster_intensity")
@@ -403,8 +421,8 @@ def visual_counts(ref, img, margin=20, sync=True):
     sync=False the device int64[3] tensor."""
     if ref.dtype != torch.uint8 or img.dtype != torch.uint8 or ref.shape != img.shape or ref.dim() != 2:
         raise ValueError("ref and img must be uint8 images of the same (height, width)")
-    if not (ref.is_contiguous() and img.is_contiguous()) or ref.device != img.device:
-        raise ValueError("ref and img must be contiguous and on one device")
+    if not (ref.is_contiguous() and img.is_contiguous()) or ref.device != img.device or not ref.is_cuda:
+        raise ValueError("ref and img must be contiguous and on one CUDA device")
     counts = torch.empty(3, dtype=torch.int64, device=ref.device)
     h, w = ref.shape
     _check(lib.mmlttb_visual_counts(ref.data_ptr(), img.data_ptr(), w, h, margin, counts.data_ptr(),
@@ -429,6 +447,8 @@ lib.mmlttb_diag_wait_timeout.argtypes = [_int, _vp, _sz, _vp]
 def diag_wait_timeout(which, workspace):
     """Run a bounded barrier wait that nothing satisfies (mmlttb_diag_wait_timeout);
     afterwards workspace_status(workspace) reports bit 1.  Asynchronous (about 2 s)."""
+    if not workspace.is_cuda:
+        raise ValueError("workspace must be a CUDA tensor")
     _check(lib.mmlttb_diag_wait_timeout(which, workspace.data_ptr(), workspace.numel() * workspace.element_size(),
                                         _stream(workspace.device)), "mmlttb_diag_wait_timeout")
 
@@ -505,6 +525,7 @@ class Batch:
         for i, s in enumerate(series):
             y, x = s["y"], s.get("x")
             _check_inputs(y, x)
+            _on(y, self.device, "every series' y")
             op = _OPS[s.get("op", "minmaxlttb")]
             r_ps = int(s.get("r_ps", 4))
             n, n_out = y.numel(), int(s["n_out"])
@@ -536,7 +557,7 @@ class Batch:
         b = ctypes.c_size_t(0)
         _check(lib.mmlttb_batch_workspace_bytes(h, ctypes.byref(b)), "mmlttb_batch_workspace_bytes")
         self.workspace_bytes = b.value
-        self.workspace = workspace if workspace is not None else torch.empty(
+        self.workspace = _on(workspace, self.device, "workspace") if workspace is not None else torch.empty(
             self.workspace_bytes, dtype=torch.uint8, device=self.device)
 
     def run(self, graph=False):
