@@ -2,6 +2,7 @@
 least one pin catches each: the pins are strong enough to trust the oracle."""
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -21,6 +22,23 @@ MUTANTS = [
     ("mean_uses_x_for_y", "sy = sy + y_at(y, ydt, IDX(p));", "sy = sy + x_at(x, xk, IDX(p));"),
     ("next_bucket_is_current", "if (j + 1 < K) { nlo = hi; nhi = part_start(j + 2, N, K); }",
      "if (j + 1 < K) { nlo = lo; nhi = hi; }"),
+    # R6: one fused multiply-add in place of the separately rounded products, either way round
+    ("area_fma_second_product_rounded", "double area = fabs((xa - xc) * (yb - ya) - (xa - xb) * (yc - ya));",
+     "double area = fabs(fma(xa - xc, yb - ya, -((xa - xb) * (yc - ya))));"),
+    ("area_fma_first_product_rounded", "double area = fabs((xa - xc) * (yb - ya) - (xa - xb) * (yc - ya));",
+     "double area = fabs(fma(-(xa - xb), yc - ya, (xa - xc) * (yb - ya)));"),
+    # R7: the next bucket summed in another order, or compensated
+    ("mean_right_to_left", "for (int64_t p = nlo; p < nhi; p++) {\n            sx = sx + x_at(x, xk, IDX(p));",
+     "for (int64_t p = nhi - 1; p >= nlo; p--) {\n            sx = sx + x_at(x, xk, IDX(p));"),
+    ("mean_compensated_sum",  # Neumaier's compensated sum: exact on most buckets
+     "double sx = 0.0, sy = 0.0;\n        for (int64_t p = nlo; p < nhi; p++) {\n            sx = sx + x_at(x, xk, IDX(p));\n"
+     "            sy = sy + y_at(y, ydt, IDX(p));\n        }\n        double cnt = (double)(nhi - nlo);\n"
+     "        double xc = sx / cnt, yc = sy / cnt;",
+     "double sx = 0.0, sy = 0.0, comp = 0.0;\n        for (int64_t p = nlo; p < nhi; p++) {\n"
+     "            sx = sx + x_at(x, xk, IDX(p));\n"
+     "            double v = y_at(y, ydt, IDX(p)), t = sy + v;\n"
+     "            comp += fabs(sy) >= fabs(v) ? (sy - t) + v : (v - t) + sy;\n            sy = t;\n        }\n"
+     "        double cnt = (double)(nhi - nlo);\n        double xc = sx / cnt, yc = (sy + comp) / cnt;"),
     ("lttb_tie_last_wins", "if (p == lo || area > best)", "if (p == lo || area >= best)"),
     ("previous_pick_not_advanced", "        a = pick;\n", "\n"),
     ("bucket_start_ceil", "return (int64_t)(num / (uint64_t)c) + 1;",
@@ -63,14 +81,14 @@ MUTANTS = [
 ]
 
 
-def _build_mutant(tmpdir, name, old, new):
+def _build_mutant(tmpdir, name, old, new, cflags=CFLAGS):
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutant {name}: anchor text found {src.count(old)} times"
     path_c = os.path.join(tmpdir, f"{name}.c")
     path_so = os.path.join(tmpdir, f"lib{name}.so")
     with open(path_c, "w") as f:
         f.write(src.replace(old, new))
-    subprocess.run(["gcc", *CFLAGS, path_c, "-o", path_so, "-lm"], check=True)
+    subprocess.run(["gcc", *cflags, path_c, "-o", path_so, "-lm"], check=True)
     return path_so
 
 
@@ -96,15 +114,39 @@ print(json.dumps(caught))
 """
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(tmpdir, name, old, new):
-    so = _build_mutant(tmpdir, name, old, new)
+def _caught(so):
     here = os.path.dirname(os.path.abspath(__file__))
-    # A child process: a mutant that writes out of bounds may crash, which also
-    # counts as detected.
     r = subprocess.run([sys.executable, "-c", _CHILD, so, here, os.path.dirname(here)],
                        capture_output=True, text=True, timeout=600)
     if r.returncode != 0:
-        return
-    caught = json.loads(r.stdout.strip().splitlines()[-1])
-    assert caught, f"no pin detects the planted mistake {name}"
+        return ["<crashed>"]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_has_fma():
+    if platform.machine() in ("aarch64", "arm64"):
+        return True  # every AArch64 core has FMADD
+    try:
+        return " fma " in open("/proc/cpuinfo").read().replace("\n", " ")
+    except OSError:
+        return False
+
+
+@pytest.mark.skipif(not _cpu_has_fma(), reason="this CPU has no FMA instruction to contract into")
+def test_contracting_build_is_caught(tmpdir):
+    """The unmodified oracle compiled the way a careless build would be: GCC's
+    default contraction (fused multiply-add wherever a product feeds a sum), with
+    FMA instructions available.  Reading R6 forbids it; the pins must notice."""
+    flags = [f for f in CFLAGS if f != "-ffp-contract=off"] + ["-ffp-contract=fast"]
+    if platform.machine() == "x86_64":
+        flags.append("-mfma")
+    so = _build_mutant(tmpdir, "contracting_build", "double area", "double area", cflags=flags)
+    assert "check_worked_examples" in _caught(so)
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmpdir, name, old, new):
+    # A child process: a mutant that writes out of bounds may crash, which also
+    # counts as detected.
+    so = _build_mutant(tmpdir, name, old, new)
+    assert _caught(so), f"no pin detects the planted mistake {name}"
