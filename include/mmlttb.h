@@ -161,11 +161,12 @@ int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64
 /*
  * MinMaxLTTB without a workspace argument and without any allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate
- * device memory when they need a result -- code running while a CUDA stream is
- * being captured, latency-critical loops that forbid cudaMalloc/cudaFree because
- * those can synchronize the whole device, and plugin hosts that offer no
- * allocator.  Same arguments, semantics and results as mmlttb_minmaxlttb, minus
- * the workspace pair; the caller still provides the inputs and out_idx/out_count.
+ * device memory when they need a result -- latency-critical loops that forbid
+ * cudaMalloc/cudaFree because those can synchronize the whole device and stall
+ * unrelated streams, and plugin hosts (a database function, a chart-server
+ * extension) that offer no allocator.  Same arguments, semantics and results as
+ * mmlttb_minmaxlttb, minus the workspace pair; the caller still provides the
+ * inputs and out_idx/out_count.
  *   Scratch: a 4 MiB array compiled into the library (a static __device__
  *   variable), so every GPU that loads the library holds those 4 MiB until the
  *   process exits.  Sizes whose workspace (mmlttb_workspace_bytes) exceeds 4 MiB
@@ -178,10 +179,25 @@ int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64
  *   behind; each call clears what must start at zero.  Calls whose work overlaps on
  *   the GPU (different streams, or different host threads) race on the array and
  *   must be serialized by the caller.
+ *   Status: the status word (bounded-wait timeouts, device checks) lives in the
+ *   array too; read it with mmlttb_noalloc_status.
  */
 int mmlttb_minmaxlttb_noalloc(const void *y, int ydtype, const void *x, int xkind, int64_t n_in,
                               int64_t n_out, int32_t r_ps, int binmode, int64_t *out_idx,
                               int64_t out_cap, int64_t *out_count, mmlttb_stream stream);
+
+/*
+ * Status word of the most recent mmlttb_minmaxlttb_noalloc call on the current
+ * device (no counterpart in the paper).  The caller cannot address that entry
+ * point's scratch, so this reads the word for it: the same bits as
+ * mmlttb_workspace_status (0 = fine, 1 = a bounded device wait timed out and the
+ * indices are not valid, 2 = a device check failed).  It waits for `stream` (pass
+ * the stream of the call to check) and copies 4 bytes to the host; it allocates
+ * nothing.  The next mmlttb_minmaxlttb_noalloc call on the device clears the word.
+ * Before the first such call on the device it reports 0.  Returns MMLTTB_OK,
+ * MMLTTB_EINVAL (status NULL) or MMLTTB_ECUDA.
+ */
+int mmlttb_noalloc_status(int *status, mmlttb_stream stream);
 
 /*
  * MinMaxLTTB (Sec. 3) on HOST buffers, end to end (blocking): the setting of series
@@ -288,6 +304,10 @@ typedef struct mmlttb_server_stats {
   int64_t submitted, completed, rejected, batches, gpu_launches;
   double mean_batch;
   double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;
+  /* continuous batching: batches launched while at least one other batch of this
+     server was still in flight (enqueued and not yet completed on the device), and
+     the most batches in flight at once */
+  int64_t overlapped_batches, max_batches_in_flight;
 } mmlttb_server_stats;
 
 typedef struct mmlttb_server *mmlttb_server_t;
@@ -338,6 +358,10 @@ int mmlttb_set_timing_events(void *start_event, void *stop_event);
  * For MinMaxLTTB with x-width bins the steps are, on the split path: edge search,
  * MinMax stream, compaction, LTTB tables, LTTB chain; on the fused-tail path: edge
  * search, MinMax stream, fused tail; on the fused path: the one fused kernel.
+ * An uncaptured batch run (mmlttb_batch_run) records seven events at fixed points:
+ * after the header clear and upload, then after the edge search, the MinMax
+ * stream, the compaction, the LTTB tables, the LTTB chain and the one-CTA-per-series
+ * LTTB, whether or not each of these kernels ran for that batch.
  */
 int mmlttb_set_stage_events(void *const *events, int count);
 

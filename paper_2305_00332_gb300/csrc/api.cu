@@ -35,6 +35,8 @@ void stage_mark(cudaStream_t st) {
   if (g_stage_i < g_stage_n) cudaEventRecord(g_stage_ev[g_stage_i++], st);
 }
 
+void stage_disarm() { g_stage_n = g_stage_i = 0; }
+
 int cuda_fail(cudaError_t e) {
   g_last_cuda_error = (int)e;
   return MMLTTB_ECUDA;
@@ -741,8 +743,7 @@ int mmlttb_workspace_status(const void* workspace, int* status, mmlttb_stream st
 }  // extern "C"
 
 // ---------------------------------------------------------------- no-allocation variant
-// Some callers cannot allocate device memory at the moment they need a result: code
-// that runs while a CUDA stream is being captured (cudaMalloc is not allowed there),
+// Some callers cannot allocate device memory at the moment they need a result:
 // latency-critical loops whose owners forbid allocation because cudaMalloc/cudaFree
 // can synchronize the whole device and stall unrelated streams, and plugin hosts
 // (a database function, a chart server extension) that hand out no allocator at all.
@@ -800,4 +801,13 @@ extern "C" int mmlttb_minmaxlttb_noalloc(const void* y, int ydtype, const void* 
   // the stream before its first kernel; every other byte it reads is written first.
   return run_single(MMLTTB_OP_MINMAXLTTB, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx,
                     out_cap, out_count, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
+}
+
+extern "C" int mmlttb_noalloc_status(int* status, mmlttb_stream stream) {
+  if (!status) return MMLTTB_EINVAL;
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  // The status word is the first word of the header, as in a caller's workspace.
+  return mmlttb_workspace_status(scratch, status, stream);
 }

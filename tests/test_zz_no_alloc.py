@@ -1,8 +1,9 @@
 """mmlttb_minmaxlttb_noalloc, the entry point for callers that cannot allocate
-device memory (code inside a stream capture, allocation-free serving loops,
-plugin hosts without an allocator): through the C ABI, two calls in a row must
-return exactly the indices of the workspace entry point mmlttb_minmaxlttb, and
-sizes beyond its static scratch must be refused.  This file is collected last."""
+device memory (serving loops that forbid cudaMalloc/cudaFree because those can
+synchronize the device, plugin hosts without an allocator): through the C ABI, two
+calls in a row must return exactly the indices of the workspace entry point
+mmlttb_minmaxlttb with a clean status word (mmlttb_noalloc_status), and sizes
+beyond its static scratch must be refused.  This file is collected last."""
 import ctypes
 
 import numpy as np
@@ -23,6 +24,16 @@ def noalloc_fn(mm):
     return f
 
 
+def noalloc_status(mm):
+    f = mm.lib.mmlttb_noalloc_status
+    f.restype = _int
+    f.argtypes = [_vp, _vp]
+    v = ctypes.c_int(-1)
+    rc = f(ctypes.byref(v), torch.cuda.current_stream().cuda_stream)
+    assert rc == mm.OK, mm.strerror(rc)
+    return v.value
+
+
 def call_noalloc(mm, y, n_out, r_ps, x=None, binmode=0):
     n = y.numel()
     cap = max(min(n, n_out), 1)
@@ -41,8 +52,10 @@ def cases():
     y2 = torch.from_numpy(synth.random_walk(300_000, seed=1, dtype=np.float64)).cuda()
     x2 = torch.from_numpy(synth.exp_gaps_x(300_000, seed=1, mean_gap=50.0, big_gaps=3, big_gap=10**7)).cuda()
     y3 = torch.from_numpy(synth.random_walk(200_000, seed=2, dtype=np.float32)).cuda()
+    y4 = torch.from_numpy(synth.random_walk(10_000_000, seed=4, dtype=np.float32)).cuda()
     return [
         (y1, 1000, 4, None, 0),     # MinMax preselection + transition-table LTTB
+        (y4, 1000, 4, None, 0),     # y above 8 MiB: streaming kernel, then the fused tail
         (y2, 2000, 4, x2, 1),       # x-width bins, float64 y
         (y3, 60_000, 4, None, 0),   # r_ps * n_out >= n: LTTB on all points
         (y3, 40, 64, None, 0),      # large preselected buckets: grid-wide LTTB
@@ -56,6 +69,7 @@ def test_noalloc_equals_workspace_entry_point_twice(mm):
         for _ in range(2):  # the second call reuses scratch left by the first
             rc, out, cnt = call_noalloc(mm, y, n_out, r_ps, x, bm)
             assert rc == mm.OK, mm.strerror(rc)
+            assert noalloc_status(mm) == 0
             torch.cuda.synchronize()
             k = int(cnt.item())
             assert k == exp.numel()
@@ -68,3 +82,10 @@ def test_noalloc_refuses_sizes_beyond_its_scratch(mm):
     assert rc == mm.ESCRATCH
     torch.cuda.synchronize()
     assert int(cnt.item()) == -1 and bool((out == -1).all())
+
+
+def test_noalloc_status_rejects_a_null_pointer(mm):
+    f = mm.lib.mmlttb_noalloc_status
+    f.restype = _int
+    f.argtypes = [_vp, _vp]
+    assert f(None, torch.cuda.current_stream().cuda_stream) == mm.EINVAL
