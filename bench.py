@@ -9,7 +9,15 @@ needed between steps.
 
 Prints ONE JSON line (rank 0).  Multi-GPU runs (torchrun) are independent replicas:
 each rank downsamples its own copy, and `value` counts the points of all ranks over
-the slowest rank's time.
+the slowest rank's time.  Single-GPU runs add three sub-records measured after the
+headline, each with its own clock record (bench_workloads.py):
+  vs_plain_lttb  1e8 float32 points, n_out=2000: MinMaxLTTB at r_ps 2/4/8/16 against
+                 plain LTTB on all points on the same GPU;
+  batched        4096 series of 1e3..1e7 points in one launch sequence replayed as a
+                 CUDA graph, against 4096 single calls;
+  serving        64 resident series of 1e8 points, Poisson zoom-window requests at
+                 5k/20k/50k req/s (3 runs each): p50/p99 latency, continuous batching
+                 against one request per launch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -48,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the plain-LTTB, batched and serving sub-records")
     ap.add_argument("--workload", default="1e9-xwidth",
                     choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving", "visual"],
                     help="the headline (default) or one of the other measured workloads")
@@ -185,7 +195,8 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample_points": S},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_in": args.n, "n_out": N_OUT, "r_ps": R_PS,
+                                        "bins": "xwidth", "reference_sample_points": S},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -223,6 +234,7 @@ def main():
     gen_s = time.time() - t_gen
     y = y_h.to(dev, non_blocking=False)
     x = x_h.to(dev, non_blocking=False)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     out = torch.empty(N_OUT, dtype=torch.int64, device=dev)
     cnt = torch.empty(1, dtype=torch.int64, device=dev)
     wsb = mm.workspace_bytes(mm.OP_MINMAXLTTB, mm.F64, mm.X_I64, n, N_OUT, R_PS, mm.BINS_XWIDTH)
@@ -243,7 +255,6 @@ def main():
         a.record(stream)
         b.record(stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     clocks = ClockSampler(vis[local] if local < len(vis) else str(local))
     clocks.start()
     time.sleep(0.3)
@@ -344,6 +355,26 @@ def main():
                "sample": f"the full workload once ({n} points), single-threaded C oracle"}
         parity = "bit-exact" if np.array_equal(ref, res) else "MISMATCH"
 
+    # the metric's other parts, on this GPU after the headline (single-GPU runs only):
+    # MinMaxLTTB against plain GPU LTTB, the 4096-series batch, and the served stream
+    subs = {}
+    if ws == 1 and not args.headline_only:
+        del y_h, x_h
+        import bench_workloads as bw
+        clock_index = vis[local] if local < len(vis) else str(local)
+        sub_steps, sub_warm = K, max(3, args.warmup)
+        for key, fn in (("vs_plain_lttb", lambda: bw.record_vs_plain_lttb(mm, sub_steps, sub_warm, clock_index,
+                                                                          oracle=not args.no_cpu_baseline)),
+                        ("batched", lambda: bw.record_batched(mm, sub_steps, sub_warm, clock_index,
+                                                              oracle=not args.no_cpu_baseline)),
+                        ("serving", lambda: bw.record_serving(mm, clock_index))):
+            t_sub = time.time()
+            try:
+                subs[key] = fn()
+            except Exception as e:  # reported in the line; the headline stands on its own
+                subs[key] = {"error": f"{type(e).__name__}: {e}"}
+            subs[key]["wall_s"] = round(time.time() - t_sub, 1)
+
     value = job_rate(n, ws, ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
@@ -364,6 +395,7 @@ def main():
         "clocks": clk,
         "parity_vs_oracle": parity,
         "status_word": status,
+        **subs,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -385,12 +417,16 @@ def _code_only(text):
 
 
 def stream_source_hash():
-    """sha256[:16] of the streaming kernel's sources, comments removed."""
+    """sha256[:16] of the streaming kernel's sources, comments removed, and of the
+    constants (#define lines) of the public header they include; the header's function
+    declarations do not reach the kernel."""
     import hashlib
     h = hashlib.sha256()
     paths = [os.path.join(ROOT, "paper_2305_00332_gb300", "csrc", f) for f in STREAM_SOURCES]
-    for path in paths + [os.path.join(ROOT, "include", "mmlttb.h")]:
+    for path in paths:
         h.update(_code_only(open(path).read()).encode())
+    header = _code_only(open(os.path.join(ROOT, "include", "mmlttb.h")).read())
+    h.update("\n".join(ln for ln in header.splitlines() if ln.lstrip().startswith("#define")).encode())
     return h.hexdigest()[:16]
 
 

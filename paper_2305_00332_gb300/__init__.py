@@ -601,7 +601,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", _i64), ("completed", _i64), ("rejected", _i64), ("batches", _i64),
                 ("gpu_launches", _i64), ("mean_batch", ctypes.c_double), ("latency_p50_s", ctypes.c_double),
                 ("latency_p99_s", ctypes.c_double), ("latency_max_s", ctypes.c_double),
-                ("latency_mean_s", ctypes.c_double)]
+                ("latency_mean_s", ctypes.c_double), ("overlapped_batches", _i64),
+                ("max_batches_in_flight", _i64)]
 
 
 lib.mmlttb_server_pool_bytes.restype = _int

@@ -215,8 +215,14 @@ static Batch batch_args(const BatchImpl* b, void* ws) {
   return bt;
 }
 
-// Enqueue the whole batch on `st`: upload, then the kernels (capturable).
+// Enqueue the whole batch on `st`: upload, then the kernels (capturable).  An armed
+// set of stage events (mmlttb_set_stage_events, uncaptured runs) is recorded at seven
+// fixed points: after the upload, then after the edge search, the stream, the
+// compaction, the tables, the chain and the block engine, whether or not each ran.
 int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
+  struct StageReset {  // the stage events are one-shot: disarm when this call returns
+    ~StageReset() { stage_disarm(); }
+  } stage_reset;
   if (b->bound_ws != ws) batch_bind(b, ws);
   const Batch bt = batch_args(b, ws);
   cudaError_t e;
@@ -224,30 +230,37 @@ int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
   if ((e = cudaMemcpyAsync((char*)ws + b->off_plans, b->pinned, b->upload_bytes,
                            cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e);
+  stage_mark(st);
   const int nb = (int)b->n;
   if (bt.total_edges > 0) {
     if ((e = launch_edges(bt, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
+  stage_mark(st);
   if (b->W > 0) {
     const int64_t grid = (b->W + kStreamWarps - 1) / kStreamWarps;
     if ((e = launch_stream(bt, grid, b->variant, b->ymode, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
+  stage_mark(st);
   if (b->total_bin_ctas > 0) {
     if ((e = launch_compact(bt, st)) != cudaSuccess) return cuda_fail(e);
     g_launches += 3;
   }
+  stage_mark(st);
   if (bt.total_slots > 0) {
     if ((e = launch_tables(bt, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
+  stage_mark(st);
   if ((e = launch_chain(bt, nb, b->max_tab, st)) != cudaSuccess) return cuda_fail(e);
   ++g_launches;
+  stage_mark(st);
   if (b->any_block) {
     if ((e = launch_lttb_block(bt, nb, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
+  stage_mark(st);
   return MMLTTB_OK;
 }
 

@@ -13,6 +13,8 @@ extern thread_local unsigned long long g_launches;  // kernels launched by this 
 
 // Record the next armed per-stage profiling event (if any) on `st`.
 void stage_mark(cudaStream_t st);
+// Disarm the per-stage profiling events (they are one-shot per call).
+void stage_disarm();
 // Remember `e` as the thread's last CUDA error and return MMLTTB_ECUDA.
 int cuda_fail(cudaError_t e);
 

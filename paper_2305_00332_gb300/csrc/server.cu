@@ -83,6 +83,7 @@ struct mmlttb_server {
   // statistics since the last reset
   std::vector<double> lat;
   int64_t batches = 0, batched_requests = 0, submitted = 0, rejected = 0;
+  int64_t overlapped_batches = 0, max_in_flight = 0;
   unsigned long long launches = 0;
   int last_error = MMLTTB_OK;
 };
@@ -225,6 +226,11 @@ void scheduler(mmlttb_server* s) {
         r.state = RQ_RUNNING;
         s->pending.pop_front();
       }
+      // batches still in flight on the other slots when this one is admitted
+      int64_t others = 0;
+      for (Slot* o : s->slots) others += (o != sl && o->busy) ? 1 : 0;
+      if (others > 0) s->overlapped_batches += 1;
+      s->max_in_flight = std::max<int64_t>(s->max_in_flight, others + 1);
       sl->ids = ids;
       sl->busy = true;
       sl->done.store(false);
@@ -427,6 +433,8 @@ int mmlttb_server_get_stats(mmlttb_server_t s, mmlttb_server_stats* st) {
   st->batches = s->batches;
   st->mean_batch = s->batches ? (double)s->batched_requests / (double)s->batches : 0.0;
   st->gpu_launches = (int64_t)s->launches;
+  st->overlapped_batches = s->overlapped_batches;
+  st->max_batches_in_flight = s->max_in_flight;
   if (!s->lat.empty()) {
     std::vector<double> v = s->lat;
     std::sort(v.begin(), v.end());
@@ -446,6 +454,7 @@ int mmlttb_server_reset_stats(mmlttb_server_t s) {
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat.clear();
   s->batches = s->batched_requests = s->submitted = s->rejected = 0;
+  s->overlapped_batches = s->max_in_flight = 0;
   s->launches = 0;
   return MMLTTB_OK;
 }

@@ -40,45 +40,54 @@ def _map(fn, items):
         return list(ex.map(fn, items))
 
 
-def _walk_ends(n, seed, sigma):
-    """Per-chunk offsets: the walk's value just before each chunk starts."""
-    def end(k_ab):
-        k, (a, b) = k_ab
-        s = _rng(seed, TAG_STEPS, k).standard_normal(b - a)
-        if sigma != 1.0:
-            s *= sigma
-        return np.cumsum(s)[-1]
-    chunks = _chunks(n)
-    ends = _map(end, list(enumerate(chunks)))
-    offs = [0.0]
-    for e in ends[:-1]:
-        offs.append(offs[-1] + e)  # sequential FP64
-    return chunks, offs
+def _steps(seed, sigma, k, m):
+    s = _rng(seed, TAG_STEPS, k).standard_normal(m)
+    if sigma != 1.0:
+        s *= sigma
+    return s
 
 
 def random_walk(n, seed=0, dtype=np.float32, sigma=1.0, out=None, extra=None):
     """Gaussian random walk y[i] = sum_{k<=i} s_k, s_k ~ N(0, sigma^2), FP64, stored as dtype.
 
-    extra(a, b, v) may add further FP64 terms to the chunk v = y[a:b] before rounding."""
+    extra(a, b, v) may add further FP64 terms to the chunk v = y[a:b] before rounding.
+    Each chunk's steps are drawn once: the chunk-local FP64 cumulative sums are kept
+    (in `out` itself for float64 output, else in a temporary float64 array) until the
+    offsets of the chunks before them are known."""
     n = int(n)
     if out is None:
         out = np.empty(n, dtype=dtype)
     if n == 0:
         return out
-    chunks, offs = _walk_ends(n, seed, sigma)
+    chunks = _chunks(n)
+    tmp = out if out.dtype == np.float64 else np.empty(n, np.float64)
+
+    def local(k_ab):
+        k, (a, b) = k_ab
+        np.cumsum(_steps(seed, sigma, k, b - a), out=tmp[a:b])
+        return tmp[b - 1]
+    ends = _map(local, list(enumerate(chunks)))
+    offs = [0.0]
+    for e in ends[:-1]:
+        offs.append(offs[-1] + e)  # sequential FP64
 
     def fill(k_ab):
         k, (a, b) = k_ab
-        s = _rng(seed, TAG_STEPS, k).standard_normal(b - a)
-        if sigma != 1.0:
-            s *= sigma
-        v = np.cumsum(s)
+        v = tmp[a:b]
         v += offs[k]
         if extra is not None:
             extra(a, b, v)
-        out[a:b] = v
+        if tmp is not out:
+            out[a:b] = v
     _map(fill, list(enumerate(chunks)))
     return out
+
+
+def random_walks(lengths, seed0, dtype=np.float32):
+    """Independent walks random_walk(lengths[i], seed=seed0 + i), generated on a pool
+    of threads (many short series, each a single chunk)."""
+    return _map(lambda i_n: random_walk(int(i_n[1]), seed=seed0 + i_n[0], dtype=dtype),
+                list(enumerate(lengths)))
 
 
 def walk_sines_spikes(n, seed=0, dtype=np.float32, periods=(1e3, 1e5, 1e7), spike_p=1e-4,

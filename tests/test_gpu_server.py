@@ -133,3 +133,28 @@ def test_malformed_oversize_and_full_queue(mm, resident):
     for i in ids:
         assert len(srv.wait(i)[0]) == 100
     srv.close()
+
+
+def test_batches_overlap_on_the_device(mm, resident):
+    """Continuous batching, not a queue: under a burst, batches are admitted while
+    other batches of the same server are still in flight on the device (the
+    server counts them at admission), and results stay those of single calls.  A
+    one-slot server never overlaps, so the count is not trivially positive."""
+    reqs = make_requests(4, 240, [2_000_000, 1_000_000, 500_000], 1)
+    srv, _ = start_server(mm, resident, streams=3, max_batch=8, workspace_bytes_per_stream=128 << 20)
+    ids = [srv.submit(*q) for q in reqs]  # a burst: the queue fills faster than slots free up
+    res = [srv.wait(i)[0] for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["batches"] >= 240 // 8
+    assert st["overlapped_batches"] > 0
+    assert 2 <= st["max_batches_in_flight"] <= 3
+    for q, got in zip(reqs[::8], res[::8]):
+        assert np.array_equal(got, single(mm, resident, q)), q
+    one, _ = start_server(mm, resident, streams=1, max_batch=8, workspace_bytes_per_stream=128 << 20)
+    ids = [one.submit(*q) for q in reqs[:64]]
+    for i in ids:
+        one.wait(i)
+    st1 = one.stats()
+    one.close()
+    assert st1["overlapped_batches"] == 0 and st1["max_batches_in_flight"] == 1
