@@ -4,8 +4,8 @@
 // Launch sequences for one series (all on the caller's stream, no host sync), by
 // launch path (single_path):
 //   split:       memset(header) -> [k_edges] -> k_stream -> k_bins -> k_binscan ->
-//                k_place -> k_tables -> k_chain (k_lttb_grid / k_lttb_block instead of
-//                the table pair when LTTB buckets are large)
+//                k_place -> k_tables -> k_chain, or, when LTTB buckets are large,
+//                [k_chain] -> k_lttb_means -> k_lttb_fix (a batch: k_lttb_block)
 //   fused tail:  [k_edges] -> k_stream -> k_fused<0> (compaction and LTTB, one launch)
 //   fused:       memset(header) -> k_fused<1> (the whole call in one persistent launch)
 // or k_iota when every index is kept.
@@ -59,7 +59,6 @@ int get_dev_info(DevInfo* out) {
   e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(e);
   for (int v = 0; v < kStreamVariants; ++v) d.stream_bps[v] = stream_blocks_per_sm(v);
-  d.grid_bps = lttb_grid_blocks_per_sm();
   d.fused_grid = fused_grid_size(d.sms);
   d.ok = true;
   if (dev >= 0 && dev < 64) g_dev[dev] = d;
@@ -97,8 +96,7 @@ int64_t stream_warps(const DevInfo& d, int variant, int64_t work) {
 struct SinglePlan {
   int32_t branch = BR_ARANGE, engine = EN_NONE;
   int64_t B = 0, K = 0, npos = 0, W = 0, Wcap = 0, tab_cap = 0;
-  int grid_lttb = 0;
-  size_t off_edges = 0, off_rec = 0, off_sel = 0, off_tab = 0, off_means = 0, off_partial = 0;
+  size_t off_edges = 0, off_rec = 0, off_sel = 0, off_tab = 0, off_means = 0;
   size_t off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, off_px = 0, off_py = 0;
   size_t off_ftot = 0;
   int64_t nct = 0;  // compaction CTAs
@@ -216,11 +214,8 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
       p.off_tab = off;
       off = align256(off + (size_t)mcap);
     } else {
-      p.grid_lttb = d.sms * d.grid_bps;
-      p.off_means = off;
-      off = align256(off + (size_t)p.K * 16);
-      p.off_partial = off;
-      off = align256(off + (size_t)p.grid_lttb * 32);
+      p.off_means = off;  // means, bucket statistics, picks and worklists of the large-bucket engine
+      off = align256(off + lttb_big_bytes(p.K));
     }
   }
   p.total = off;
@@ -321,7 +316,6 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   bt.total_slots = p.tab_cap;  // k_tables: one slot per position
   bt.rec = p.off_rec ? (Record*)(w + p.off_rec) : nullptr;
   bt.edges = p.off_edges ? (int64_t*)(w + p.off_edges) : nullptr;
-  bt.partial = p.off_partial ? (double*)(w + p.off_partial) : nullptr;
   bt.total_bin_ctas = p.nct;
   bt.binres = p.off_binres ? (int64_t*)(w + p.off_binres) : nullptr;
   bt.cta_sum = p.off_ctasum ? (int32_t*)(w + p.off_ctasum) : nullptr;
@@ -418,7 +412,12 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
       if ((e = launch_chain(bt, 1, 0, st)) != cudaSuccess) return cuda_fail(e);
       ++g_launches;
     }
-    if ((e = launch_lttb_grid(bt, p.grid_lttb, st)) != cudaSuccess) return cuda_fail(e);
+    // the means and bucket statistics on every SM, then the chain as a fixpoint
+    if ((e = launch_lttb_means(bt, d.sms, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
+    ++g_launches;
+    if ((e = launch_lttb_fix(bt, d.sms, st)) != cudaSuccess) return cuda_fail(e);
+    stage_mark(st);
     ++g_launches;
   }
   return MMLTTB_OK;

@@ -1,0 +1,159 @@
+// FP32 bounds on the FP64 LTTB triangle area (reading R6), so that an argmax over a
+// large bucket needs FP64 only where two candidates come close.
+//
+// The area the method compares is A(b) = fl|fl(fl(P*fl(yb-ya)) - fl(fl(xa-xb)*R))|
+// with P = fl(xa-xc), R = fl(yc-ya), every FP64 operation rounded on its own.  This part
+// has about 1.6 FP64 lane operations per cycle and SM against about 76 FP32 adds, and
+// FP64 <-> FP32 or int64 -> FP32 conversions run at FP64 speed, so an FP64 area per
+// candidate would dominate.  StepBound (below) gives, for every candidate of a bucket,
+// an FP32 value |T| formed from values converted with integer operations only, and one
+// error bound E for the whole bucket with |A(b) - |T|| <= E; its comment carries the
+// error analysis.  Over a bucket, a candidate whose |T| + E is below the largest |T| - E
+// has a strictly smaller area than the candidate attaining it: it can neither win nor
+// tie.  When only one candidate remains it is the pick; otherwise the FP64 area
+// (tri_area) decides among the remaining ones, with the lowest position on ties (R8),
+// which is the sequential result.
+#pragma once
+
+#include "common.cuh"
+
+namespace mmlttb {
+namespace {
+
+constexpr float kFilterU = 5.9604644775390625e-08f;  // 2^-24
+constexpr float kFilterAbs = 7.888609052210118e-31f;  // 2^-100
+
+// FP32 value of an int64, exact below 2^22 in magnitude, else truncated (relative
+// error below 2^-23).  Integer operations and one FP32 add only.
+__device__ __forceinline__ float f32_of_i64(long long d) {
+  if (d > -(1ll << 22) && d < (1ll << 22))  // 1.5*2^23 + d holds d exactly in its low bits
+    return __fsub_rn(__int_as_float(0x4B400000 + (int)d), 12582912.0f);
+  const unsigned long long a = d < 0 ? 0ull - (unsigned long long)d : (unsigned long long)d;
+  const int lz = __clzll((long long)a);
+  const unsigned mant = (unsigned)((a << lz) >> 40) & 0x7fffffu;  // 23 bits below the leading one
+  const unsigned bits = ((unsigned)(63 - lz + 127) << 23) | mant | (d < 0 ? 0x80000000u : 0u);
+  return __uint_as_float(bits);
+}
+
+// Whether a float is zero or in [2^-60, 2^60) in magnitude.
+__device__ __forceinline__ bool f32_in_range(float v) {
+  const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+  const unsigned e = b >> 23;
+  return b == 0u || (e >= 127u - 60u && e < 127u + 60u);
+}
+
+// FP64 -> FP32 by truncation of the significand (relative error below 2^-23), with
+// integer operations only; *ok turns false outside {0} and [2^-60, 2^60).
+__device__ __forceinline__ float f32_of_f64(double v, bool* ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int be = (int)((b >> 52) & 0x7ff);
+  if ((b & 0x7fffffffffffffffull) == 0) return __uint_as_float(sign);
+  const int e = be - 1023;
+  if (be == 0 || e < -60 || e >= 60) {  // subnormal, tiny, huge, inf or NaN
+    *ok = false;
+    return 0.0f;
+  }
+  return __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// int64 value of an integer-valued double below 2^63 in magnitude (exact; integer
+// operations only).
+__device__ __forceinline__ long long i64_of_f64_int(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7ff);
+  if (be < 1023) return 0;  // |v| < 1: an integer-valued double is 0
+  const unsigned long long sig = (b & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = be - 1075;
+  const unsigned long long a = sh >= 0 ? sig << sh : sig >> (-sh);
+  return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+// A bucket mean as the FP32 filter uses it: x = xint + xfrac (xint = floor of the FP64
+// mean, xfrac its fraction rounded to FP32) and y truncated to FP32 (NaN when outside
+// the filter's range).  Only integer x (implicit or int64) is filtered.
+struct MeanF {
+  long long xint;
+  float xfrac, y32;
+};
+
+// FP32 truncation of a double known to be below 2^60 in magnitude; values below 2^-60
+// become 0 (absolute error below 2^-60).  Monotone non-decreasing.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (e < -60) return __uint_as_float(sign);
+  return __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// Per-bucket statistics for the step bound below: the smallest and largest y of the
+// bucket as the filter sees them (float32 y exactly, float64 y truncated by f32_trunc,
+// which is monotone, so every candidate's FP32 y lies between them; NaN when a value is
+// NaN or not below 2^60 in magnitude), and the x span x_last - x_first (exact integer;
+// for implicit x the position span), and its first x (the origin of the step bound).
+struct BucketF {
+  float ymin, ymax;
+  long long xspan, x0;
+};
+
+// One error bound for every candidate of a bucket (a step of a long chain).  With the
+// bucket's first x as origin (xb' = xb - x0, xa' = xa - x0, exact integers):
+//   area expression  P (yb - ya) + R (xb - xa) = P dy + R xb' + K0,  K0 = -R xa'
+//   per candidate    T = fma(P32, fl32(yb32 - ya32), fma(R32, xb'32, K32)),
+//                    K32 = -fl32(R32 xa'32)
+// and |A(b) - |T|| <= E for every candidate of the bucket, with
+//   Dm = max(ymax - ya32, ya32 - ymin)             (bounds |yb32 - ya32|)
+//   Xm = X' + |xa'32|                                (bounds |xb - xa|, X' the x span)
+//   tY = 2^-22 (max(|ymin|, |ymax|) + |ya32|) for truncated float64 y, else 0
+//   M  = (|P32|+eP)(Dm + tY) + (|R32|+eR) Xm
+//   E  = (10u + rho) M + 1.02 (eP (Dm + tY) + eR Xm) + (|P32|+eP)(tY + 2^-59) + 2^-100
+// The terms: the FP32 roundings of dy, the two FMAs and K32, each at most u M (10u
+// leaves room for the FP64 roundings of A, 3.01 2^-53 M); x differences truncated
+// beyond 2^22 (rho = 2^-22, on both xb' and xa'); the errors eP, eR of P32, R32
+// (AreaBound::init_split); truncation of float64 y (tY) and float64 y below 2^-60 taken
+// as 0 (2^-59 for yb and ya); subnormal results (2^-100).  The step is unfiltered unless
+// P32, R32, the bucket's y range, X' and the pick's values are below 2^60, so M stays far
+// from overflow.  Ordering a bucket's candidates by |T| orders their upper bounds.
+struct StepBound {
+  float P32, R32, K32, ya32, E;
+  bool ok;
+
+  __device__ __forceinline__ void init(long long xa, float ya, long long x0, const MeanF& c, const BucketF& bk,
+                                       bool y_trunc) {
+    const float big = 1.152921504606847e18f;  // 2^60
+    const float d32 = f32_of_i64(xa - c.xint);
+    P32 = __fsub_rn(d32, c.xfrac);
+    R32 = __fsub_rn(c.y32, ya);
+    ya32 = ya;
+    const float xa32 = f32_of_i64(xa - x0);
+    const float xs = f32_of_i64(bk.xspan);
+    const float aP = fabsf(P32), aR = fabsf(R32);
+    ok = fabsf(ya) < big && fabsf(c.y32) < big && fabsf(d32) < big && aP < big && aR < big &&
+         fabsf(bk.ymin) < big && fabsf(bk.ymax) < big && fabsf(xa32) < big && xs < big && c.xfrac >= 0.0f &&
+         c.xfrac < 1.0f;
+    K32 = -__fmul_rn(R32, xa32);
+    const float eP = __fmaf_ru(4.0f * kFilterU, fabsf(d32), __fmaf_ru(2.0f * kFilterU, aP, kFilterU));
+    const float eR = __fmaf_ru(4.0f * kFilterU, fabsf(c.y32),
+                               __fmaf_ru(y_trunc ? 4.0f * kFilterU : 0.0f, fabsf(ya), __fmul_ru(2.0f * kFilterU, aR)));
+    const float dm = fmaxf(__fsub_ru(bk.ymax, ya), __fsub_ru(ya, bk.ymin));
+    const float tY = y_trunc ? __fmul_ru(4.0f * kFilterU, __fadd_ru(fmaxf(fabsf(bk.ymin), fabsf(bk.ymax)), fabsf(ya)))
+                             : 0.0f;
+    const float xm = __fadd_ru(xs, fabsf(xa32));
+    const float pP = __fadd_ru(aP, eP), pR = __fadd_ru(aR, eR);
+    const float dmt = __fadd_ru(dm, tY);
+    const float M = __fmaf_ru(pP, dmt, __fmul_ru(pR, xm));
+    float e = __fmul_ru(14.0f * kFilterU, M);
+    e = __fmaf_ru(1.02f, __fmaf_ru(eP, dmt, __fmul_ru(eR, xm)), e);
+    e = __fmaf_ru(pP, __fadd_ru(tY, 1.7347234759768071e-18f), e);  // 2^-59
+    E = __fadd_ru(e, kFilterAbs);
+    ok = ok && E < 3.0e38f;
+  }
+  // |T| of a candidate (see above)
+  __device__ __forceinline__ float t_abs(float yb, float xb_rel) const {
+    return fabsf(__fmaf_rn(P32, __fsub_rn(yb, ya32), __fmaf_rn(R32, xb_rel, K32)));
+  }
+};
+
+}  // namespace
+}  // namespace mmlttb

@@ -137,7 +137,6 @@ struct Batch {
   unsigned* status;    // error bits (1: a bounded wait timed out, 2: device check failed)
   unsigned* barrier;   // grid barrier counter (EN_GRID and the fused kernel)
   int64_t* fused_tot;  // per CTA of the fused kernel: indices its bins emit
-  double* partial;     // 2 x grid x (area, position) partials (EN_GRID)
   int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
   int32_t zero_status; // the launch clears the status and barrier words first (first kernel of a call)
   int32_t tab_rounds;  // k_tables: rounds of 32 slots per warp (1..kTableRounds)
@@ -456,7 +455,12 @@ cudaError_t launch_compact(const Batch& bt, cudaStream_t st);
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st);
 cudaError_t launch_chain(const Batch& bt, int n_blocks, int64_t max_positions, cudaStream_t st);
 cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_t st);
-cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st);
+// Large-bucket LTTB of the single series bt.one (lttb_big.cu): the next-bucket means and
+// bucket statistics on every SM, then the chain as a fixpoint over all SMs (cooperative
+// launch).  lttb_big_bytes(K): the workspace both need at sp.means.
+cudaError_t launch_lttb_means(const Batch& bt, int sms, cudaStream_t st);
+cudaError_t launch_lttb_fix(const Batch& bt, int sms, cudaStream_t st);
+size_t lttb_big_bytes(int64_t K);
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st);
 int stream_blocks_per_sm(int variant);
 // Fused single-series kernel, one CTA per SM (fused.cu): its grid on a device with
@@ -473,7 +477,6 @@ __device__ __forceinline__ void zero_header(const Batch& bt) {
   *bt.status = 0u;
   *bt.barrier = 0u;
 }
-int lttb_grid_blocks_per_sm();
 constexpr int kGridThreads = 256;
 
 }  // namespace mmlttb

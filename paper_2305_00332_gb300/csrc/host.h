@@ -22,7 +22,6 @@ struct DevInfo {
   int device = 0;
   int sms = 0;
   int stream_bps[kStreamVariants] = {};  // resident stream CTAs per SM, per variant
-  int grid_bps = 0;
   int fused_grid = 0;  // CTAs of the fused single-series kernel (0: unavailable)
   bool ok = false;
 };

@@ -2,8 +2,8 @@
 //
 // Small buckets (lttb.cuh): k_tables fills one transition-table entry per position,
 // k_chain resolves the chain by a parallel prefix over function composition.
-// Large buckets use k_lttb_grid: one grid-wide argmax per bucket (cooperative
-// launch, bounded spin barrier), or k_lttb_block: one CTA per series.
+// Large buckets of a single series use lttb_big.cu; in a batch, k_lttb_block runs one
+// CTA per series.
 #include "lttb.cuh"
 
 namespace mmlttb {
@@ -40,41 +40,6 @@ __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__
   chain_series<kChainThreads>(plan_of(bt, blockIdx.x), s_tab4, bt.chain_smem, F, dom);
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier on a monotone counter with a 2 s bound.  Returns false (and
-// sets status bit 1) when the other CTAs did not all arrive in time.
-__device__ bool grid_barrier(unsigned* ctr, unsigned target, unsigned* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(ctr, 1u);
-    ok = 1;
-    const unsigned long long t0 = global_ns();
-    while (ld_acquire(ctr) < target) {
-      if (global_ns() - t0 > 2000000000ull) {
-        set_status(status, 1u);
-        ok = 0;
-        break;
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 // Failure-detection probe: a two-CTA launch in which CTA 1 never arrives, so CTA 0's
 // grid_barrier wait runs out (2 s), sets status bit 1 and the kernel returns.
 __global__ void k_barrier_probe(unsigned* ctr, unsigned* status) {
@@ -109,69 +74,6 @@ __device__ void block_argmax(long long& ab, long long& pos) {
   __syncthreads();
   ab = s_ab[0];
   pos = s_pos[0];
-}
-
-// Sequential LTTB with one grid-wide argmax per bucket (single series).
-__global__ void __launch_bounds__(kGridThreads) k_lttb_grid(const __grid_constant__ Batch bt) {
-  const SeriesPlan& sp = bt.one;
-  const int64_t m = lttb_m(sp);
-  if (m <= sp.n_out) return;  // k_chain copied the points
-  const int64_t K = sp.n_out - 2, N = m - 2;
-  const int64_t G = gridDim.x, c = blockIdx.x;
-  // Phase A: every next-bucket mean, one warp per bucket, dealt round-robin over the
-  // CTAs (bucket_mean_warp: lane-parallel when the sums are exact in any order, else
-  // the sequential sums of one lane).
-  const int lane = threadIdx.x & 31;
-  const int64_t wpb = blockDim.x >> 5;
-  for (int64_t j = (int64_t)(threadIdx.x >> 5) * G + c; j < K; j += G * wpb) {
-    int64_t lo, hi;
-    next_bucket(j, sp.dK, N, m, &lo, &hi);
-    double xc, yc;
-    bucket_mean_warp(sp, lo, hi, lane, &xc, &yc);
-    if (lane == 0) {
-      sp.means[2 * j] = xc;
-      sp.means[2 * j + 1] = yc;
-    }
-  }
-  if (!grid_barrier(bt.barrier, (unsigned)G, bt.status)) return;
-  __shared__ long long s_pick;
-  int64_t a = 0;
-  long long* part = (long long*)bt.partial;
-  for (int64_t j = 0; j < K; ++j) {
-    const int64_t lj = part_start(j, N, sp.dK), lj1 = part_start(j + 1, N, sp.dK);
-    const int64_t len = lj1 - lj;
-    const int64_t q0 = lj + muldiv(c, len, G), q1 = lj + muldiv(c + 1, len, G);
-    const double xc = sp.means[2 * j], yc = sp.means[2 * j + 1];
-    const int64_t ia = index_of(sp, a);
-    const double xa = x_of(sp, ia), ya = y_of(sp, ia);
-    long long ab = -1, pos = LLONG_MAX;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      const int64_t ib = index_of(sp, q);
-      const long long v = __double_as_longlong(tri_area(xa, ya, x_of(sp, ib), y_of(sp, ib), xc, yc));
-      if (v > ab) { ab = v; pos = q; }  // increasing q: strict keeps the first
-    }
-    block_argmax(ab, pos);
-    long long* pj = part + (j & 1) * 2 * G;
-    if (threadIdx.x == 0) { pj[2 * c] = ab; pj[2 * c + 1] = pos; }
-    if (!grid_barrier(bt.barrier, (unsigned)((j + 2) * G), bt.status)) return;
-    ab = -1;
-    pos = LLONG_MAX;
-    for (int64_t k = threadIdx.x; k < G; k += blockDim.x) {
-      const long long oab = ((volatile long long*)pj)[2 * k];
-      const long long opos = ((volatile long long*)pj)[2 * k + 1];
-      if (oab > ab || (oab == ab && opos < pos)) { ab = oab; pos = opos; }
-    }
-    block_argmax(ab, pos);
-    if (threadIdx.x == 0) s_pick = pos;
-    __syncthreads();
-    a = s_pick;
-    if (c == 0 && threadIdx.x == 0) sp.out[j + 1] = index_of(sp, a);
-  }
-  if (c == 0 && threadIdx.x == 0) {
-    sp.out[0] = index_of(sp, 0);
-    sp.out[K + 1] = index_of(sp, m - 1);
-    if (sp.out_count) *sp.out_count = sp.n_out;
-  }
 }
 
 // Sequential LTTB with one CTA per series (batched series with large buckets).
@@ -233,14 +135,6 @@ cudaError_t launch_barrier_probe(const Batch& bt, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int lttb_grid_blocks_per_sm() {
-  int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_lttb_grid, kGridThreads, 0) != cudaSuccess)
-    return 1;
-  if (bps > 2) bps = 2;
-  return bps > 0 ? bps : 1;
-}
-
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st) {
   if (bt.total_slots <= 0) return cudaSuccess;
   // as many rounds per warp as keep about 16 warps per SM busy, at most kTableRounds
@@ -280,13 +174,6 @@ cudaError_t launch_iota(int64_t* out, int64_t n, int64_t* out_count, cudaStream_
   if (blocks < 1) blocks = 1;
   k_iota<<<(unsigned)blocks, 256, 0, st>>>(out, n, out_count);
   return cudaGetLastError();
-}
-
-cudaError_t launch_lttb_grid(const Batch& bt, int grid, cudaStream_t st) {
-  Batch copy = bt;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)k_lttb_grid, dim3(grid), dim3(kGridThreads), args,
-                                     0, st);
 }
 
 cudaError_t launch_lttb_block(const Batch& bt, int n_blocks, cudaStream_t st) {

@@ -20,6 +20,41 @@
 namespace mmlttb {
 namespace {
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a monotone counter with a 2 s bound.  Returns false (and
+// sets status bit 1) when the other CTAs did not all arrive in time.
+__device__ bool grid_barrier(unsigned* ctr, unsigned target, unsigned* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    ok = 1;
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire(ctr) < target) {
+      if (global_ns() - t0 > 2000000000ull) {
+        set_status(status, 1u);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 __device__ __forceinline__ int64_t lttb_m(const SeriesPlan& sp) {
   return sp.branch == BR_LTTB_ALL ? sp.n : *sp.m_ptr;
 }

@@ -1,7 +1,7 @@
 """GPU path vs the oracle, index array by index array (bit-exact), through the C ABI.
 
 Small sweeps cover every branch (arange, plain LTTB, MinMax + LTTB, preselect only),
-both LTTB engines (transition tables; grid-wide steps), both bin modes, float32 and
+both LTTB engines (transition tables; the large-bucket fixpoint engine), both bin modes, float32 and
 float64 y, implicit / int64 / float64 x, ties, signed zeros, constant series, empty
 and degenerate sizes, and misaligned y pointers.  Full-size cases follow the
 workloads the method is measured on."""
@@ -177,7 +177,7 @@ def test_table_engine_threshold(mm, ref):
 
 
 def test_grid_engine_large_buckets(mm, ref):
-    """Plain LTTB with buckets of ~1e4..5e5 points (grid-wide steps)."""
+    """Plain LTTB with buckets of ~1e4..5e5 points (the large-bucket fixpoint engine)."""
     y = synth.random_walk(1_000_003, seed=9, dtype=np.float32)
     yd = dev(y)
     for n_out in (3, 4, 100, 1000):
