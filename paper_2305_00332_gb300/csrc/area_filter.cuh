@@ -70,12 +70,60 @@ __device__ __forceinline__ long long i64_of_f64_int(double v) {
 }
 
 // A bucket mean as the FP32 filter uses it: x = xint + xfrac (xint = floor of the FP64
-// mean, xfrac its fraction rounded to FP32) and y truncated to FP32 (NaN when outside
+// mean, xfrac its fraction in FP32 within 2^-22) and y truncated to FP32 (NaN when outside
 // the filter's range).  Only integer x (implicit or int64) is filtered.
 struct MeanF {
   long long xint;
   float xfrac, y32;
 };
+
+// Whether |v| < 2^k for a double (integer test of the exponent field; false for inf
+// and NaN), k in [-1022, 1023].
+__device__ __forceinline__ bool f64_below_pow2(double v, int k) {
+  const int be = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
+  return be < 1023 + k;
+}
+
+// The split form of an FP64 mean with integer operations: xint = floor(v), and the
+// fraction v - xint in [0, 1) as FP32 with an absolute error below 2^-22 (truncated
+// significand bits, and for negative v one FP32 subtraction from 1).  *ok turns false
+// unless |v| < 2^52.
+__device__ __forceinline__ void split_floor(double v, long long* xint, float* xfrac, bool* ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const bool neg = (b >> 63) != 0;
+  if (e >= 52) {  // integer-valued, or beyond the filter's range
+    *ok = false;
+    *xint = 0;
+    *xfrac = 0.0f;
+    return;
+  }
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+  unsigned long long ip, fb;
+  int fe;  // fraction = fb * 2^fe
+  if (e < 0) {
+    ip = 0;
+    fb = (b & 0x7fffffffffffffffull) ? m : 0;  // |v| < 1 (zero or subnormal: fraction |v|)
+    fe = (e < -1022 ? -1022 : e) - 52;
+    if (((b >> 52) & 0x7ff) == 0) fb = b & 0xfffffffffffffull;
+  } else {
+    ip = m >> (52 - e);
+    fb = m & ((1ull << (52 - e)) - 1);
+    fe = e - 52;
+  }
+  // fb * 2^fe in FP32: truncate fb, scale by a power of two (exact unless far below 2^-126)
+  float f = f32_of_i64((long long)fb);
+  const int se = fe < -126 ? -126 : fe;
+  f = __fmul_rn(f, __uint_as_float((unsigned)(se + 127) << 23));
+  if (fe < -126) f = 0.0f;  // below 2^-126: the fraction's error stays below 2^-100
+  if (!neg) {
+    *xint = (long long)ip;
+    *xfrac = f;
+  } else {
+    *xint = -(long long)ip - (fb ? 1 : 0);
+    *xfrac = fb ? __fsub_rn(1.0f, f) : 0.0f;
+  }
+}
 
 // FP32 truncation of a double known to be below 2^60 in magnitude; values below 2^-60
 // become 0 (absolute error below 2^-60).  Monotone non-decreasing.
@@ -110,11 +158,17 @@ struct BucketF {
 //   E  = (10u + rho) M + 1.02 (eP (Dm + tY) + eR Xm) + (|P32|+eP)(tY + 2^-59) + 2^-100
 // The terms: the FP32 roundings of dy, the two FMAs and K32, each at most u M (10u
 // leaves room for the FP64 roundings of A, 3.01 2^-53 M); x differences truncated
-// beyond 2^22 (rho = 2^-22, on both xb' and xa'); the errors eP, eR of P32, R32
-// (AreaBound::init_split); truncation of float64 y (tY) and float64 y below 2^-60 taken
+// beyond 2^22 (rho = 2^-22, on both xb' and xa'); the errors eP, eR of P32, R32 (below);
+// truncation of float64 y (tY) and float64 y below 2^-60 taken
 // as 0 (2^-59 for yb and ya); subnormal results (2^-100).  The step is unfiltered unless
 // P32, R32, the bucket's y range, X' and the pick's values are below 2^60, so M stays far
 // from overflow.  Ordering a bucket's candidates by |T| orders their upper bounds.
+// P32 = fl32(f32(xa - xint) - xfrac) and R32 = fl32(yc32 - ya32) (the mean c in the
+// split form of MeanF) carry absolute error bounds against the FP64 values P, R:
+//   eP = 2^-22 |f32(xa - xint)| + 2^-23 |P32| + 2^-22   (truncation of the integer
+//        difference, rounding of the subtraction and FP64 rounding of P, the fraction)
+//   eR = 2^-22 |yc32| + tau' |ya32| + 2^-23 |R32|         (truncations of the mean and the
+//        pick's y, tau' = 2^-22 for float64 y and 0 for float32; the two roundings)
 struct StepBound {
   float P32, R32, K32, ya32, E;
   bool ok;
@@ -133,7 +187,7 @@ struct StepBound {
          fabsf(bk.ymin) < big && fabsf(bk.ymax) < big && fabsf(xa32) < big && xs < big && c.xfrac >= 0.0f &&
          c.xfrac < 1.0f;
     K32 = -__fmul_rn(R32, xa32);
-    const float eP = __fmaf_ru(4.0f * kFilterU, fabsf(d32), __fmaf_ru(2.0f * kFilterU, aP, kFilterU));
+    const float eP = __fmaf_ru(4.0f * kFilterU, fabsf(d32), __fmaf_ru(2.0f * kFilterU, aP, 4.0f * kFilterU));
     const float eR = __fmaf_ru(4.0f * kFilterU, fabsf(c.y32),
                                __fmaf_ru(y_trunc ? 4.0f * kFilterU : 0.0f, fabsf(ya), __fmul_ru(2.0f * kFilterU, aR)));
     const float dm = fmaxf(__fsub_ru(bk.ymax, ya), __fsub_ru(ya, bk.ymin));
@@ -154,6 +208,26 @@ struct StepBound {
     return fabsf(__fmaf_rn(P32, __fsub_rn(yb, ya32), __fmaf_rn(R32, xb_rel, K32)));
   }
 };
+
+// The x of position p as an exact integer for the filter (implicit x: the index).
+__device__ __forceinline__ long long filter_x(const SeriesPlan& sp, int64_t p) {
+  if (sp.xk == MMLTTB_X_IMPLICIT) return sp.sel ? sp.sel[p] : p;
+  if (sp.xk == MMLTTB_X_I64) return sp.px ? i64_of_f64_int(sp.px[p]) : __ldg((const long long*)sp.x + p);
+  return 0;  // float64 x is not filtered
+}
+
+// The y of position p as the chain's FP32 filter sees it (float32 exactly, float64
+// truncated), with a flag for values the filter cannot take (NaN, beyond 2^60).
+__device__ __forceinline__ float filter_y(const SeriesPlan& sp, int64_t p, bool* ok) {
+  if (!sp.py && sp.ydt == MMLTTB_F32) {
+    const float v = __ldg((const float*)sp.y + p);
+    *ok = *ok && fabsf(v) < 1.152921504606847e18f;
+    return v;
+  }
+  const double v = sp.py ? __ldg(sp.py + p) : __ldg((const double*)sp.y + p);
+  *ok = *ok && f64_below_pow2(v, 60);
+  return f32_trunc(v);
+}
 
 }  // namespace
 }  // namespace mmlttb

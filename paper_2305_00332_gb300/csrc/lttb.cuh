@@ -15,6 +15,7 @@
 //                  writes the picked indices.
 #pragma once
 
+#include "area_filter.cuh"
 #include "common.cuh"
 
 namespace mmlttb {
@@ -182,6 +183,76 @@ __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N,
   }
 }
 
+// The pick in bucket [lo, hi) after the point (xa, ya) at position p, against the mean
+// (xc, yc) of the bucket after it: the offset of the point with the largest FP64 area
+// (tri_area), the lowest offset on ties (R6, R8).  With integer x the candidates are
+// first bounded in FP32 (StepBound over this bucket: its y range and x span from the
+// candidates themselves, the mean split as the filter needs it); when the first one's
+// lower bound exceeds every other upper bound it is the pick without any FP64 area,
+// otherwise the FP64 areas of the candidates that may be largest decide.  One thread.
+__device__ int table_pick(const SeriesPlan& sp, double xa, double ya, double xc, double yc, int64_t lo, int64_t hi) {
+  StepBound sb;
+  sb.ok = false;
+  float thr = -INFINITY;
+  long long x0 = 0;
+  if (sp.xk != MMLTTB_X_F64 && f64_below_pow2(xa, 53)) {
+    // (integer tests of the exponent fields: no FP64 instruction on this path)
+    bool ok = f64_below_pow2(ya, 60) && f64_below_pow2(yc, 60);
+    float ymin = INFINITY, ymax = -INFINITY;
+    for (int64_t q = lo; q < hi; ++q) {
+      const float v = filter_y(sp, q, &ok);
+      ymin = fminf(ymin, v);
+      ymax = fmaxf(ymax, v);
+    }
+    x0 = filter_x(sp, lo);
+    const long long xl = filter_x(sp, hi - 1);
+    const long long lim = 1ll << 53;
+    ok = ok && x0 > -lim && x0 < lim && xl > -lim && xl < lim;
+    MeanF c;
+    split_floor(xc, &c.xint, &c.xfrac, &ok);
+    if (ok) {
+      c.y32 = f32_trunc(yc);
+      BucketF bk;
+      bk.ymin = ymin;
+      bk.ymax = ymax;
+      bk.x0 = x0;
+      bk.xspan = xl - x0;
+      sb.init(i64_of_f64_int(xa), f32_trunc(ya), x0, c, bk, sp.ydt != MMLTTB_F32);
+    }
+    if (sb.ok) {
+      float t1 = -1.0f, t2 = -1.0f;
+      int p1 = 0;
+      for (int64_t q = lo; q < hi; ++q) {
+        bool qok = true;
+        const float ta = sb.t_abs(filter_y(sp, q, &qok), f32_of_i64(filter_x(sp, q) - x0));
+        t2 = fmaxf(t2, fminf(ta, t1));
+        if (ta > t1) {
+          t1 = ta;
+          p1 = (int)(q - lo);
+        }
+      }
+      if (__fadd_ru(t2, sb.E) < __fsub_rd(t1, sb.E)) return p1;  // decided without FP64
+      thr = __fsub_rd(__fsub_rd(t1, sb.E), sb.E);
+    }
+  }
+  long long best = -1;  // bits of a non-negative double order like the double
+  int pick = 0;
+  for (int64_t q = lo; q < hi; ++q) {
+    if (sb.ok) {
+      bool qok = true;
+      if (!(sb.t_abs(filter_y(sp, q, &qok), f32_of_i64(filter_x(sp, q) - x0)) >= thr)) continue;
+    }
+    double xb, yb;
+    pos_xy(sp, q, &xb, &yb);
+    const long long ab = __double_as_longlong(tri_area(xa, ya, xb, yb, xc, yc));
+    if (best < 0 || ab > best) {  // R8: the first largest wins
+      best = ab;
+      pick = (int)(q - lo);
+    }
+  }
+  return pick;
+}
+
 // Slots a warp of k_tables fills: up to kTableRounds rounds of 32 (bt.tab_rounds; one
 // round when there are too few slots to fill the GPU).  The next-bucket means of all
 // the buckets these slots target are formed together, one bucket per lane: an FP64
@@ -287,26 +358,7 @@ __device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, i
     double xa, ya;
     pos_xy(sp, p, &xa, &ya);
     const double2 c = mean[d];
-    long long best = -1;  // bits of a non-negative double order like the double
-    int pick = 0;
-    for (int64_t q0 = lo; q0 < hi; q0 += 4) {  // four candidates' loads in flight
-      double xb[4], yb[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        xb[u] = yb[u] = 0.0;
-        if (q0 + u < hi) pos_xy(sp, q0 + u, &xb[u], &yb[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (q0 + u >= hi) break;
-        const long long ab = __double_as_longlong(tri_area(xa, ya, xb[u], yb[u], c.x, c.y));
-        if (q0 + u == lo || ab > best) {  // R8: the first largest wins
-          best = ab;
-          pick = (int)(q0 + u - lo);
-        }
-      }
-    }
-    sp.tab[p] = (uint8_t)pick;
+    sp.tab[p] = (uint8_t)table_pick(sp, xa, ya, c.x, c.y, lo, hi);
   }
 }
 

@@ -443,26 +443,6 @@ __device__ double sum_y(const SeriesPlan& sp, int64_t lo, int64_t hi, int lane, 
 
 constexpr int kMeansThreads = 256;
 
-// The x of position p as an exact integer for the filter (implicit x: the index).
-__device__ __forceinline__ long long filter_x(const SeriesPlan& sp, int64_t p) {
-  if (sp.xk == MMLTTB_X_IMPLICIT) return sp.sel ? sp.sel[p] : p;
-  if (sp.xk == MMLTTB_X_I64) return sp.px ? i64_of_f64_int(sp.px[p]) : __ldg((const long long*)sp.x + p);
-  return 0;  // float64 x is not filtered
-}
-
-// The y of position p as the chain's FP32 filter sees it (float32 exactly, float64
-// truncated), with a flag for values the filter cannot take (NaN, beyond 2^60).
-__device__ __forceinline__ float filter_y(const SeriesPlan& sp, int64_t p, bool* ok) {
-  if (!sp.py && sp.ydt == MMLTTB_F32) {
-    const float v = __ldg((const float*)sp.y + p);
-    *ok = *ok && fabsf(v) < 1.152921504606847e18f;
-    return v;
-  }
-  const double v = sp.py ? __ldg(sp.py + p) : __ldg((const double*)sp.y + p);
-  *ok = *ok && fabs(v) < 1.152921504606847e18;
-  return f32_trunc(v);
-}
-
 // For t in [0, K]: bucket t's statistics for the chain's filter (t < K) and the mean
 // after bucket t-1, that is of bucket t or, for t = K, of the last point (R1, R5, R7):
 // means[2(t-1)], means[2(t-1)+1] and their split form.  A warp per t; bucket t's y is
@@ -512,11 +492,10 @@ __global__ void __launch_bounds__(kMeansThreads) k_lttb_means(const __grid_const
       sp.means[2 * (t - 1) + 1] = yc;
       // the split form the chain's FP32 filter uses (integer x)
       MeanF f;
-      const double fl = floor(xc);
-      const bool fits = fabs(fl) < 9007199254740992.0;
-      f.xint = fits ? (long long)fl : 0;
-      f.xfrac = fits ? (float)__dsub_rn(xc, fl) : __int_as_float(0x7fc00000);  // NaN: unfiltered
-      f.y32 = fabs(yc) < 1.152921504606847e18 ? f32_trunc(yc) : __int_as_float(0x7fc00000);
+      bool fits = true;
+      split_floor(xc, &f.xint, &f.xfrac, &fits);
+      if (!fits) f.xfrac = __int_as_float(0x7fc00000);  // NaN: unfiltered
+      f.y32 = f64_below_pow2(yc, 60) ? f32_trunc(yc) : __int_as_float(0x7fc00000);
       mf[t - 1] = f;
     }
   }
