@@ -69,12 +69,13 @@ __device__ __forceinline__ long long i64_of_f64_int(double v) {
   return (b >> 63) ? -(long long)a : (long long)a;
 }
 
-// A bucket mean as the FP32 filter uses it: x = xint + xfrac (xint = floor of the FP64
-// mean, xfrac its fraction in FP32 within 2^-22) and y truncated to FP32 (NaN when outside
-// the filter's range).  Only integer x (implicit or int64) is filtered.
+// A bucket mean as the FP32 filter uses it, with error bounds against the FP64 mean
+// (xc, yc) the method forms (R7): |xint + xfrac - xc| <= ex and |y32 - yc| <= ey, xfrac
+// in [0, 1) (NaN, or y32 NaN, when the filter cannot take this mean).  Only integer x
+// (implicit or int64) is filtered.
 struct MeanF {
   long long xint;
-  float xfrac, y32;
+  float xfrac, y32, ex, ey;
 };
 
 // Whether |v| < 2^k for a double (integer test of the exponent field; false for inf
@@ -165,9 +166,9 @@ struct BucketF {
 // from overflow.  Ordering a bucket's candidates by |T| orders their upper bounds.
 // P32 = fl32(f32(xa - xint) - xfrac) and R32 = fl32(yc32 - ya32) (the mean c in the
 // split form of MeanF) carry absolute error bounds against the FP64 values P, R:
-//   eP = 2^-22 |f32(xa - xint)| + 2^-23 |P32| + 2^-22   (truncation of the integer
-//        difference, rounding of the subtraction and FP64 rounding of P, the fraction)
-//   eR = 2^-22 |yc32| + tau' |ya32| + 2^-23 |R32|         (truncations of the mean and the
+//   eP = 2^-22 |f32(xa - xint)| + 2^-23 |P32| + ex   (truncation of the integer
+//        difference; rounding of the subtraction and FP64 rounding of P; the mean's x)
+//   eR = ey + tau' |ya32| + 2^-23 |R32|                (the mean's y; truncation of the
 //        pick's y, tau' = 2^-22 for float64 y and 0 for float32; the two roundings)
 struct StepBound {
   float P32, R32, K32, ya32, E;
@@ -175,23 +176,26 @@ struct StepBound {
 
   __device__ __forceinline__ void init(long long xa, float ya, long long x0, const MeanF& c, const BucketF& bk,
                                        bool y_trunc) {
+    init_span(xa, ya, x0, c, bk.ymin, bk.ymax, f32_of_i64(bk.xspan), y_trunc);
+  }
+  // the same with the bucket's y range and FP32 x span (f32_of_i64 of the span) given
+  __device__ __forceinline__ void init_span(long long xa, float ya, long long x0, const MeanF& c, float ymin,
+                                            float ymax, float xs, bool y_trunc) {
     const float big = 1.152921504606847e18f;  // 2^60
     const float d32 = f32_of_i64(xa - c.xint);
     P32 = __fsub_rn(d32, c.xfrac);
     R32 = __fsub_rn(c.y32, ya);
     ya32 = ya;
     const float xa32 = f32_of_i64(xa - x0);
-    const float xs = f32_of_i64(bk.xspan);
     const float aP = fabsf(P32), aR = fabsf(R32);
     ok = fabsf(ya) < big && fabsf(c.y32) < big && fabsf(d32) < big && aP < big && aR < big &&
-         fabsf(bk.ymin) < big && fabsf(bk.ymax) < big && fabsf(xa32) < big && xs < big && c.xfrac >= 0.0f &&
-         c.xfrac < 1.0f;
+         fabsf(ymin) < big && fabsf(ymax) < big && fabsf(xa32) < big && xs < big && c.xfrac >= 0.0f &&
+         c.xfrac < 1.0f && c.ex < 1.0f && c.ey < big;
     K32 = -__fmul_rn(R32, xa32);
-    const float eP = __fmaf_ru(4.0f * kFilterU, fabsf(d32), __fmaf_ru(2.0f * kFilterU, aP, 4.0f * kFilterU));
-    const float eR = __fmaf_ru(4.0f * kFilterU, fabsf(c.y32),
-                               __fmaf_ru(y_trunc ? 4.0f * kFilterU : 0.0f, fabsf(ya), __fmul_ru(2.0f * kFilterU, aR)));
-    const float dm = fmaxf(__fsub_ru(bk.ymax, ya), __fsub_ru(ya, bk.ymin));
-    const float tY = y_trunc ? __fmul_ru(4.0f * kFilterU, __fadd_ru(fmaxf(fabsf(bk.ymin), fabsf(bk.ymax)), fabsf(ya)))
+    const float eP = __fmaf_ru(4.0f * kFilterU, fabsf(d32), __fmaf_ru(2.0f * kFilterU, aP, c.ex));
+    const float eR = __fmaf_ru(y_trunc ? 4.0f * kFilterU : 0.0f, fabsf(ya), __fmaf_ru(2.0f * kFilterU, aR, c.ey));
+    const float dm = fmaxf(__fsub_ru(ymax, ya), __fsub_ru(ya, ymin));
+    const float tY = y_trunc ? __fmul_ru(4.0f * kFilterU, __fadd_ru(fmaxf(fabsf(ymin), fabsf(ymax)), fabsf(ya)))
                              : 0.0f;
     const float xm = __fadd_ru(xs, fabsf(xa32));
     const float pP = __fadd_ru(aP, eP), pR = __fadd_ru(aR, eR);
@@ -227,6 +231,61 @@ __device__ __forceinline__ float filter_y(const SeriesPlan& sp, int64_t p, bool*
   const double v = sp.py ? __ldg(sp.py + p) : __ldg((const double*)sp.y + p);
   *ok = *ok && f64_below_pow2(v, 60);
   return f32_trunc(v);
+}
+
+// The filter form of the FP64 mean (xc, yc) of positions [lo, hi) (R7), without an
+// FP64 instruction.  With integer x below 2^45 and at most 255 positions, every
+// partial FP64 x sum is an integer below 2^53, so the FP64 sum is the exact integer
+// sum S and xc = fl64(S/n): xint = floor(S/n) by integer division, xfrac = fl32(r/n)
+// with r = S - n*xint, and ex = 2^-24 (the fraction) + 2^-53 |xc|.  The y sum runs
+// left to right in FP32 over the filter's y (float32 exact, float64 truncated with
+// relative error tau < 2^-23); against the FP64 mean, with A = max |y|:
+//   |fl32 sum - sum of filter y| <= gamma32(n-1) n A,  |that - exact sum| <= tau n A,
+//   |exact sum - FP64 sum| <= gamma64(n-1) n A,  and the two divisions contribute
+//   2^-24 |y32| and 2^-53 |yc|,
+// so ey = 2^-24 |y32| + (n 2^-24 + tau + 2^-44)(1 + 2^-10) A' covers them (A' the largest
+// |filter y|; gamma(k) = k u / (1 - k u); the last factor covers A <= A' (1 + 2^-22)
+// and gamma's denominator).  False when the filter cannot take the mean.
+__device__ __forceinline__ bool mean_filter_form(const SeriesPlan& sp, int64_t lo, int64_t hi, MeanF* c) {
+  const long long n = hi - lo;
+  if (sp.xk == MMLTTB_X_F64 || n <= 0 || n > 255) return false;
+  bool ok = true;
+  unsigned long long sx = 0, xmax = 0;  // two's complement sum: exact once |x| < 2^45 is known
+  float sy = 0.0f, amax = 0.0f;
+  for (int64_t p = lo; p < hi; ++p) {
+    const long long x = filter_x(sp, p);
+    const unsigned long long ax = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    xmax = ax > xmax ? ax : xmax;
+    sx += (unsigned long long)x;
+    const float v = filter_y(sp, p, &ok);
+    amax = fmaxf(amax, fabsf(v));
+    sy = __fadd_rn(sy, v);
+  }
+  if (!ok || xmax >= (1ull << 45)) return false;
+  const long long S = (long long)sx;
+  long long q, r;
+  if (S > -(1ll << 31) && S < (1ll << 31)) {
+    const int q32 = (int)S / (int)n;
+    q = q32;
+    r = S - q * n;
+  } else {
+    q = S / n;
+    r = S - q * n;
+  }
+  if (r < 0) {
+    q -= 1;
+    r += n;
+  }
+  c->xint = q;
+  c->xfrac = __fdiv_rn((float)(int)r, (float)(int)n);  // r/n <= 254/255: below 1 after rounding
+  const unsigned long long aq = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  c->ex = __fmaf_ru(2.220446049250313e-16f, f32_of_i64((long long)aq), 2.0f * kFilterU);  // 2^-52
+  c->y32 = __fdiv_rn(sy, (float)(int)n);
+  const float tau = sp.ydt != MMLTTB_F32 ? 4.0f * kFilterU : 0.0f;
+  const float cn = __fmul_ru(__fmaf_ru((float)(int)n, kFilterU, __fadd_ru(tau, 5.684341886080802e-14f)),  // 2^-44
+                             1.0009765625f);
+  c->ey = __fmaf_ru(cn, amax, __fmul_ru(kFilterU, fabsf(c->y32)));
+  return true;
 }
 
 }  // namespace

@@ -17,8 +17,7 @@ constexpr int kTableThreads = 64;  // small CTAs: the positions spread over ever
 // A warp per kTableBlock consecutive table slots (one slot per position); the warp
 // finds the series of its first slot with a 32-ary search.
 __global__ void __launch_bounds__(kTableThreads) k_tables(const __grid_constant__ Batch bt) {
-  __shared__ TableReq s_req[kTableThreads / 32][kTableBlock];
-  __shared__ double2 s_mean[kTableThreads / 32][kTableBlock];
+  __shared__ TableShared s_tab[kTableThreads / 32];
   pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -26,7 +25,7 @@ __global__ void __launch_bounds__(kTableThreads) k_tables(const __grid_constant_
   const int64_t base = ((int64_t)blockIdx.x * (kTableThreads / 32) + wid) * 32 * rounds;
   if (base >= bt.total_slots) return;
   const int s0 = bt.tab_offs ? warp_upper_index(bt.tab_offs, bt.n_series, base, lane) : 0;
-  table_block(bt, base, rounds, s0, lane, s_req[wid], s_mean[wid]);
+  table_block(bt, base, rounds, s0, lane, s_tab[wid]);
 }
 
 __global__ void __launch_bounds__(kChainThreads) k_chain(const __grid_constant__ Batch bt) {

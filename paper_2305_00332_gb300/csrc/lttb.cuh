@@ -183,89 +183,146 @@ __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N,
   }
 }
 
-// The pick in bucket [lo, hi) after the point (xa, ya) at position p, against the mean
-// (xc, yc) of the bucket after it: the offset of the point with the largest FP64 area
-// (tri_area), the lowest offset on ties (R6, R8).  With integer x the candidates are
-// first bounded in FP32 (StepBound over this bucket: its y range and x span from the
-// candidates themselves, the mean split as the filter needs it); when the first one's
-// lower bound exceeds every other upper bound it is the pick without any FP64 area,
-// otherwise the FP64 areas of the candidates that may be largest decide.  One thread.
-__device__ int table_pick(const SeriesPlan& sp, double xa, double ya, double xc, double yc, int64_t lo, int64_t hi) {
+// Slots a warp of k_tables fills: up to kTableRounds rounds of 32 (bt.tab_rounds; one
+// round when there are too few slots to fill the GPU).
+constexpr int kTableRounds = 7;
+constexpr int kTableBlock = 32 * kTableRounds;
+constexpr int kTableCache = 8;  // candidates kept in shared memory per bucket
+
+struct TableReq {  // a bucket that picks of the warp's slots fall in
+  int64_t jt;      // the bucket (its picks follow picks in bucket jt - 1)
+  int32_t s;       // series
+  int32_t o;       // offset in the block of its first slot
+};
+
+// Up to 32 buckets of a table prepared for the entries whose picks fall in them, one
+// per lane, structure of arrays (lanes that read different buckets hit different
+// banks): candidates [lo, lo + cnt), the bucket after it [nlo, nlo + ncnt) and, with
+// integer x, the FP32 filter data of StepBound: the mean after the bucket in filter
+// form (ex < 0 where the filter does not apply), the candidates' y range, x origin
+// and x span, and for buckets of up to kTableCache positions their FP32 y and x offsets.
+struct TableChunk {
+  long long lo[32], nlo[32], x0[32], xint[32];
+  int cnt[32], ncnt[32];
+  float xfrac[32], ym[32], ex[32], ey[32], ymin[32], ymax[32], xs[32];
+  float cy[kTableCache][32], cx[kTableCache][32];
+};
+
+struct TableShared {  // a warp's shared memory in k_tables
+  TableReq req[kTableBlock];
+  uint8_t dreq[kTableBlock];  // the request of each slot of the block (0xff: no entry)
+  TableChunk ch;
+};
+
+// Lane i of a chunk: bucket [lo, hi) prepared with the bucket after it [nlo, nhi),
+// using integer and FP32 operations only.
+__device__ void table_prepare(const SeriesPlan& sp, int64_t lo, int64_t hi, int64_t nlo, int64_t nhi,
+                              TableChunk& ch, int i) {
+  MeanF c;
+  bool ok = mean_filter_form(sp, nlo, nhi, &c);
+  float ymin = INFINITY, ymax = -INFINITY;
+  const long long x0 = filter_x(sp, lo);
+  const bool cached = hi - lo <= kTableCache;
+  for (int64_t q = lo; q < hi; ++q) {
+    const float v = filter_y(sp, q, &ok);
+    ymin = fminf(ymin, v);
+    ymax = fmaxf(ymax, v);
+    if (cached) {
+      ch.cy[q - lo][i] = v;
+      ch.cx[q - lo][i] = f32_of_i64(filter_x(sp, q) - x0);
+    }
+  }
+  const long long xl = filter_x(sp, hi - 1), lim = 1ll << 53;
+  ok = ok && x0 > -lim && x0 < lim && xl > -lim && xl < lim;
+  ch.lo[i] = lo;
+  ch.nlo[i] = nlo;
+  ch.cnt[i] = (int)(hi - lo);
+  ch.ncnt[i] = (int)(nhi - nlo);
+  ch.x0[i] = x0;
+  ch.xint[i] = c.xint;
+  ch.xfrac[i] = c.xfrac;
+  ch.ym[i] = c.y32;
+  ch.ex[i] = ok ? c.ex : -1.0f;
+  ch.ey[i] = c.ey;
+  ch.ymin[i] = ymin;
+  ch.ymax[i] = ymax;
+  ch.xs[i] = f32_of_i64(xl - x0);
+}
+
+// The offset in bucket i of the chunk of the pick after position pa: the largest FP64
+// area (tri_area), the lowest offset on ties (R6, R8).  FP32 bounds first (StepBound);
+// when the first candidate's lower bound exceeds every other upper bound it is the
+// pick without any FP64 operation, otherwise the FP64 mean (R7) and the FP64 areas of
+// the candidates that may be largest decide.
+__device__ int table_pick(const SeriesPlan& sp, const TableChunk& ch, int i, int64_t pa) {
+  const int64_t lo = ch.lo[i];
+  const int cnt = ch.cnt[i];
+  const long long x0 = ch.x0[i];
   StepBound sb;
   sb.ok = false;
   float thr = -INFINITY;
-  long long x0 = 0;
-  if (sp.xk != MMLTTB_X_F64 && f64_below_pow2(xa, 53)) {
-    // (integer tests of the exponent fields: no FP64 instruction on this path)
-    bool ok = f64_below_pow2(ya, 60) && f64_below_pow2(yc, 60);
-    float ymin = INFINITY, ymax = -INFINITY;
-    for (int64_t q = lo; q < hi; ++q) {
-      const float v = filter_y(sp, q, &ok);
-      ymin = fminf(ymin, v);
-      ymax = fmaxf(ymax, v);
-    }
-    x0 = filter_x(sp, lo);
-    const long long xl = filter_x(sp, hi - 1);
-    const long long lim = 1ll << 53;
-    ok = ok && x0 > -lim && x0 < lim && xl > -lim && xl < lim;
-    MeanF c;
-    split_floor(xc, &c.xint, &c.xfrac, &ok);
-    if (ok) {
-      c.y32 = f32_trunc(yc);
-      BucketF bk;
-      bk.ymin = ymin;
-      bk.ymax = ymax;
-      bk.x0 = x0;
-      bk.xspan = xl - x0;
-      sb.init(i64_of_f64_int(xa), f32_trunc(ya), x0, c, bk, sp.ydt != MMLTTB_F32);
-    }
-    if (sb.ok) {
-      float t1 = -1.0f, t2 = -1.0f;
-      int p1 = 0;
-      for (int64_t q = lo; q < hi; ++q) {
-        bool qok = true;
-        const float ta = sb.t_abs(filter_y(sp, q, &qok), f32_of_i64(filter_x(sp, q) - x0));
-        t2 = fmaxf(t2, fminf(ta, t1));
-        if (ta > t1) {
-          t1 = ta;
-          p1 = (int)(q - lo);
+  if (ch.ex[i] >= 0.0f) {
+    bool aok = true;
+    const long long xa = filter_x(sp, pa);
+    const float ya = filter_y(sp, pa, &aok);
+    if (aok && xa > -(1ll << 53) && xa < (1ll << 53)) {
+      MeanF c;
+      c.xint = ch.xint[i];
+      c.xfrac = ch.xfrac[i];
+      c.y32 = ch.ym[i];
+      c.ex = ch.ex[i];
+      c.ey = ch.ey[i];
+      sb.init_span(xa, ya, x0, c, ch.ymin[i], ch.ymax[i], ch.xs[i], sp.ydt != MMLTTB_F32);
+      if (sb.ok) {
+        float t1 = -1.0f, t2 = -1.0f;
+        int p1 = 0;
+        if (cnt <= kTableCache) {
+#pragma unroll
+          for (int u = 0; u < kTableCache; ++u) {
+            if (u >= cnt) break;
+            const float ta = sb.t_abs(ch.cy[u][i], ch.cx[u][i]);
+            t2 = fmaxf(t2, fminf(ta, t1));
+            if (ta > t1) {
+              t1 = ta;
+              p1 = u;
+            }
+          }
+        } else {
+          for (int u = 0; u < cnt; ++u) {
+            bool qok = true;
+            const float ta = sb.t_abs(filter_y(sp, lo + u, &qok), f32_of_i64(filter_x(sp, lo + u) - x0));
+            t2 = fmaxf(t2, fminf(ta, t1));
+            if (ta > t1) {
+              t1 = ta;
+              p1 = u;
+            }
+          }
         }
+        if (__fadd_ru(t2, sb.E) < __fsub_rd(t1, sb.E)) return p1;  // decided without FP64
+        thr = __fsub_rd(__fsub_rd(t1, sb.E), sb.E);
       }
-      if (__fadd_ru(t2, sb.E) < __fsub_rd(t1, sb.E)) return p1;  // decided without FP64
-      thr = __fsub_rd(__fsub_rd(t1, sb.E), sb.E);
     }
   }
+  double xc, yc, xa, ya;
+  bucket_mean(sp, ch.nlo[i], ch.nlo[i] + ch.ncnt[i], &xc, &yc);
+  pos_xy(sp, pa, &xa, &ya);
   long long best = -1;  // bits of a non-negative double order like the double
-  int pick = 0;
-  for (int64_t q = lo; q < hi; ++q) {
+  int pk = 0;
+  for (int u = 0; u < cnt; ++u) {
     if (sb.ok) {
       bool qok = true;
-      if (!(sb.t_abs(filter_y(sp, q, &qok), f32_of_i64(filter_x(sp, q) - x0)) >= thr)) continue;
+      if (!(sb.t_abs(filter_y(sp, lo + u, &qok), f32_of_i64(filter_x(sp, lo + u) - x0)) >= thr)) continue;
     }
     double xb, yb;
-    pos_xy(sp, q, &xb, &yb);
+    pos_xy(sp, lo + u, &xb, &yb);
     const long long ab = __double_as_longlong(tri_area(xa, ya, xb, yb, xc, yc));
     if (best < 0 || ab > best) {  // R8: the first largest wins
       best = ab;
-      pick = (int)(q - lo);
+      pk = u;
     }
   }
-  return pick;
+  return pk;
 }
-
-// Slots a warp of k_tables fills: up to kTableRounds rounds of 32 (bt.tab_rounds; one
-// round when there are too few slots to fill the GPU).  The next-bucket means of all
-// the buckets these slots target are formed together, one bucket per lane: an FP64
-// instruction costs the FP64 pipe the same whether one lane or 32 execute it, and a
-// round of 32 positions holds only about 32/r_ps buckets.
-constexpr int kTableRounds = 7;
-constexpr int kTableBlock = 32 * kTableRounds;
-
-struct TableReq {  // a bucket whose next-bucket mean the warp needs
-  int64_t jt;      // the bucket (its picks follow picks in bucket jt - 1)
-  int32_t s;       // series
-  int32_t pad;
-};
 
 // Table slot `slot` (one slot per position of every series, series s holding slots
 // from tab_offs[s]): whether it has an entry, and the bucket jt whose pick follows a
@@ -287,19 +344,16 @@ __device__ __forceinline__ bool slot_bucket(const Batch& bt, int64_t slot, int s
 }
 
 // Table entries of the warp's block of slots [base, base + 32*rounds).  Warp-
-// collective; `s0` is the series of slot `base`; req/mean are the warp's shared
-// memory (kTableBlock entries each).
-__device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, int lane, TableReq* req,
-                            double2* mean) {
+// collective; `s0` is the series of slot `base`; sh is the warp's shared memory.
+__device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, int lane, TableShared& sh) {
   // 1. every slot's bucket; the first slot of each distinct (series, bucket) files a
-  //    request, and every slot keeps the index of its bucket's request
-  int dreq[kTableRounds];
+  //    request, and every slot notes the request it belongs to (requests follow slot
+  //    order, so that is the last one filed at or before it)
   int s = s0, nreq = 0;
   int64_t carry_jt = -1;
   int carry_s = -1;
 #pragma unroll
   for (int r = 0; r < kTableRounds; ++r) {
-    dreq[r] = -1;
     if (r >= rounds) continue;
     const int64_t slot = base + 32 * r + lane;
     if (bt.tab_offs)
@@ -317,48 +371,50 @@ __device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, i
     const unsigned fl = __ballot_sync(kFull, first);
     const int d = nreq + __popc(fl & ((2u << lane) - 1u)) - 1;
     if (first) {
-      req[d].jt = jt;
-      req[d].s = ks;
+      sh.req[d].jt = jt;
+      sh.req[d].s = ks;
+      sh.req[d].o = 32 * r + lane;
     }
-    dreq[r] = work ? d : -1;
+    sh.dreq[32 * r + lane] = work ? (uint8_t)d : (uint8_t)0xff;
     nreq += __popc(fl);
     carry_jt = __shfl_sync(kFull, work ? jt : -1, 31);
     carry_s = __shfl_sync(kFull, ks, 31);
   }
   __syncwarp();
-  // 2. the means, one bucket per lane (R5, R7)
-  for (int d = lane; d < nreq; d += 32) {
-    const TableReq q = req[d];
-    const SeriesPlan& sp = plan_of(bt, q.s);
-    const int64_t m = lttb_m(sp), K = sp.n_out - 2;
-    int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point
-    if (q.jt + 1 < K) {
-      nlo = part_start(q.jt + 1, m - 2, sp.dK);
-      nhi = part_start(q.jt + 2, m - 2, sp.dK);
+  // 2. chunks of 32 requests: one lane per bucket prepares it, with the mean of the
+  //    bucket after it (R5, R7); then one lane per slot picks (the slots of a chunk's
+  //    buckets are the block's slots from its first request's to the next chunk's)
+  for (int c0 = 0; c0 < nreq; c0 += 32) {
+    const int d = c0 + lane;
+    if (d < nreq) {
+      const TableReq q = sh.req[d];
+      const SeriesPlan& sp = plan_of(bt, q.s);
+      const int64_t m = lttb_m(sp), K = sp.n_out - 2, N = m - 2;
+      StepDiv bs;
+      bs.init(q.jt == 0 ? 0 : q.jt - 1, N, sp.dK, 1);
+      if (q.jt > 0) bs.next();
+      const int64_t lo = bs.L + 1;  // bucket jt = [lo, hi) (R1)
+      bs.next();
+      const int64_t hi = bs.L + 1;
+      int64_t nlo = m - 1, nhi = m;  // after the last bucket: the last point (R5)
+      if (q.jt + 1 < K) {
+        nlo = hi;
+        bs.next();
+        nhi = bs.L + 1;
+      }
+      table_prepare(sp, lo, hi, nlo, nhi, sh.ch, lane);
     }
-    double xc, yc;
-    bucket_mean(sp, nlo, nhi, &xc, &yc);
-    mean[d] = make_double2(xc, yc);
-  }
-  __syncwarp();
-  // 3. each slot's entry: the first largest area in bucket jt against its position
-#pragma unroll 1
-  for (int r = 0; r < rounds; ++r) {
-    const int d = dreq[r];
-    if (d < 0) continue;
-    const TableReq q = req[d];
-    const SeriesPlan& sp = plan_of(bt, q.s);
-    const int64_t p = base + 32 * r + lane - sp.tab_off;
-    const int64_t m = lttb_m(sp);
-    StepDiv bs;  // bucket jt = [lo, hi) (R1)
-    bs.init(q.jt, m - 2, sp.dK, 1);
-    const int64_t lo = bs.L + 1;
-    bs.next();
-    const int64_t hi = bs.L + 1;
-    double xa, ya;
-    pos_xy(sp, p, &xa, &ya);
-    const double2 c = mean[d];
-    sp.tab[p] = (uint8_t)table_pick(sp, xa, ya, c.x, c.y, lo, hi);
+    __syncwarp();
+    const int o0 = sh.req[c0].o;
+    const int o1 = c0 + 32 < nreq ? sh.req[c0 + 32].o : 32 * rounds;
+    for (int o = o0 + lane; o < o1; o += 32) {
+      const int dd = sh.dreq[o];
+      if (dd == 0xff) continue;
+      const SeriesPlan& sp = plan_of(bt, sh.req[dd].s);
+      const int64_t p = base + o - sp.tab_off;
+      sp.tab[p] = (uint8_t)table_pick(sp, sh.ch, dd - c0, p);
+    }
+    __syncwarp();
   }
 }
 

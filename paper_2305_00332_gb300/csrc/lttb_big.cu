@@ -496,6 +496,8 @@ __global__ void __launch_bounds__(kMeansThreads) k_lttb_means(const __grid_const
       split_floor(xc, &f.xint, &f.xfrac, &fits);
       if (!fits) f.xfrac = __int_as_float(0x7fc00000);  // NaN: unfiltered
       f.y32 = f64_below_pow2(yc, 60) ? f32_trunc(yc) : __int_as_float(0x7fc00000);
+      f.ex = 4.0f * kFilterU;                     // split_floor's fraction
+      f.ey = __fmul_ru(4.0f * kFilterU, fabsf(f.y32));  // truncation of yc
       mf[t - 1] = f;
     }
   }
