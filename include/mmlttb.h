@@ -385,6 +385,25 @@ int mmlttb_autotune(int ydtype, const void *y, int64_t n_in, int64_t n_out, int3
 int mmlttb_get_stream_variant(int ydtype, int *variant);
 int mmlttb_set_stream_variant(int ydtype, int variant);
 
+/*
+ * Staged MinMax stream (no counterpart in the paper; results are the same either way).
+ * With staging on, index bins of at most 512 bytes of float32 y (128 points) in
+ * launches that stream at least 64 MiB are read by k_stream_bulk: each warp copies
+ * tiles of whole bins (8 KiB) into shared memory with cp.async.bulk behind an mbarrier
+ * pipeline and reduces them there; other bins take the register stream (16-byte loads
+ * into registers).  Staging is off by default: on 1e8 float32 points it runs from
+ * 0.96x to 1.25x the register stream at 16- to 128-point bins and slower above, and
+ * the 4096-series batch replays 2% slower with it.  mmlttb_set_stream_staging(1)
+ * turns it on for plans made afterwards (0 turns it off); process-wide.
+ * MMLTTB_EINVAL for another value or a NULL pointer.
+ */
+int mmlttb_set_stream_staging(int enable);
+int mmlttb_get_stream_staging(int *enable);
+/* Bins per staged tile of a single-series call with these arguments on the current
+ * device (*bins_per_tile = 0: the register stream), or a negative error code. */
+int mmlttb_stream_tiles(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
+                       int64_t *bins_per_tile);
+
 /* Number of kernels this library has launched from the calling thread so far. */
 unsigned long long mmlttb_launch_count(void);
 

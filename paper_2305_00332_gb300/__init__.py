@@ -480,6 +480,35 @@ def set_single_path(path):
     _check(lib.mmlttb_set_single_path(path), "mmlttb_set_single_path")
 
 
+lib.mmlttb_set_stream_staging.argtypes = [_int]
+lib.mmlttb_get_stream_staging.argtypes = [ctypes.POINTER(_int)]
+
+
+def set_stream_staging(enable):
+    """Whether plans made from now on send small index bins of large launches to the
+    staged (cp.async.bulk) MinMax stream (True) or to the register stream (False, the
+    default)."""
+    _check(lib.mmlttb_set_stream_staging(1 if enable else 0), "mmlttb_set_stream_staging")
+
+
+def stream_staging():
+    v = _int(0)
+    _check(lib.mmlttb_get_stream_staging(ctypes.byref(v)), "mmlttb_get_stream_staging")
+    return bool(v.value)
+
+
+lib.mmlttb_stream_tiles.argtypes = [_int, _int, _int, _i64, _i64, _i32, _int, ctypes.POINTER(_i64)]
+
+
+def stream_tiles(op, ydtype, xkind, n_in, n_out, r_ps=4, binmode=BINS_INDEX):
+    """Bins per staged tile of a single-series call with these arguments here (0: the
+    register stream)."""
+    v = _i64(0)
+    _check(lib.mmlttb_stream_tiles(op, ydtype, xkind, n_in, n_out, r_ps, binmode, ctypes.byref(v)),
+           "mmlttb_stream_tiles")
+    return int(v.value)
+
+
 def single_path(op, ydtype, xkind, n_in, n_out, r_ps=4, binmode=BINS_INDEX):
     """The launch path a single-series call with these arguments takes here."""
     r = lib.mmlttb_single_path(op, ydtype, xkind, n_in, n_out, r_ps, binmode)

@@ -60,6 +60,7 @@ int get_dev_info(DevInfo* out) {
   if (e != cudaSuccess) return cuda_fail(e);
   for (int v = 0; v < kStreamVariants; ++v) d.stream_bps[v] = stream_blocks_per_sm(v);
   d.fused_grid = fused_grid_size(d.sms);
+  d.bulk_bps = stream_bulk_blocks_per_sm();
   d.ok = true;
   if (dev >= 0 && dev < 64) g_dev[dev] = d;
   *out = d;
@@ -93,6 +94,20 @@ int64_t stream_warps(const DevInfo& d, int variant, int64_t work) {
   return W;
 }
 
+int64_t bulk_warps(const DevInfo& d, int64_t tiles) {
+  const int64_t cap = (int64_t)d.sms * d.bulk_bps * kBulkWarps;
+  return tiles < cap ? tiles : cap;
+}
+
+int64_t bulk_rec_w(int64_t pos_off, int64_t total, int64_t W) {
+  if (total <= 0 || W <= 0) return 0;
+  const int64_t w = warp_of(pos_off, make_div(total), W);
+  return w < W ? w : W;
+}
+
+std::atomic<int> g_bulk_on{0};  // measured no faster overall: opt-in
+bool bulk_enabled() { return g_bulk_on.load() != 0; }
+
 struct SinglePlan {
   int32_t branch = BR_ARANGE, engine = EN_NONE;
   int64_t B = 0, K = 0, npos = 0, W = 0, Wcap = 0, tab_cap = 0;
@@ -104,6 +119,7 @@ struct SinglePlan {
   int group = 32;   // lanes per bin in the stream
   int tab_lgS = 0;  // log2 of the fused tables' slots per bucket
   int variant = 0;  // stream-kernel variant
+  int64_t bulk_bpt = 0, tcost = 0, tiles = 0, Wb = 0;  // staged stream (bulk_bpt > 0)
   size_t total = kHeader;
 };
 
@@ -171,7 +187,15 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     // x-width bins can be very uneven: keep whole warps per bin there
     const int eb = ydt == MMLTTB_F32 ? 4 : 8;
     p.group = binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(N, p.B, eb, N * eb >= kStreamThroughputBytes);
-    p.npos = series_work(N, p.B, p.group);
+    if (binmode == MMLTTB_BINS_INDEX && ydt == MMLTTB_F32 && N * eb >= kStreamThroughputBytes && bulk_enabled())
+      p.bulk_bpt = bulk_bins_per_tile(N, p.B, eb);
+    if (p.bulk_bpt > 0) {  // the staged stream: no register-stream work
+      p.group = bulk_group(p.bulk_bpt);
+      p.tiles = (p.B + p.bulk_bpt - 1) / p.bulk_bpt;
+      p.tcost = p.bulk_bpt * (((N + p.B - 1) / p.B) * eb + kBulkBinCost);
+      p.Wb = bulk_warps(d, p.tiles);
+    }
+    p.npos = p.bulk_bpt > 0 ? 0 : series_work(N, p.B, p.group);
     p.Wcap = stream_warp_cap(d);
     p.variant = stream_variant(d, ydt);
     p.W = stream_warps(d, p.variant, p.npos);
@@ -308,9 +332,16 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   sp.out = out;
   sp.out_count = out_count;
   sp.tab_lgS = p.tab_lgS;
+  sp.bulk_bpt = p.bulk_bpt;
+  sp.tcost_off = 0;
+  sp.tcost = p.tcost;
+  sp.rec_w = 0;
   set_bin_steps(sp);
   bt.total_pos = p.npos;
   bt.n_warps = p.W;
+  bt.tcost_offs = nullptr;
+  bt.total_tcost = p.tiles * p.tcost;
+  bt.n_bulk_warps = p.Wb;
   set_warp_divs(bt);
   bt.total_edges = (p.B > 0 && sp.binmode == MMLTTB_BINS_XWIDTH) ? p.B + 1 : 0;
   bt.total_slots = p.tab_cap;  // k_tables: one slot per position
@@ -334,7 +365,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     bt.dgrid = make_div(G);
     // the header words (status, barrier) are cleared by the first kernel of the
     // call, or by a memset when the fused kernel is the first
-    const bool lead = path == MMLTTB_PATH_FUSED_TAIL && (bt.total_edges > 0 || p.W > 0);
+    const bool lead = path == MMLTTB_PATH_FUSED_TAIL && (bt.total_edges > 0 || p.W > 0 || p.Wb > 0);
     if (!lead && (e = cudaMemsetAsync(ws, 0, kHeader, st)) != cudaSuccess) return cuda_fail(e);
     stage_mark(st);
     if (path == MMLTTB_PATH_FUSED) {
@@ -360,10 +391,16 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
       if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
         return cuda_fail(e);
-      stage_mark(st);
       ++g_launches;
       bt.zero_status = 0;
     }
+    if (p.Wb > 0) {
+      if ((e = launch_stream_bulk(bt, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+        return cuda_fail(e);
+      ++g_launches;
+      bt.zero_status = 0;
+    }
+    if (p.Wb > 0 || p.W > 0) stage_mark(st);
     if (g_ev_stop && (e = cudaEventRecord(g_ev_stop, st)) != cudaSuccess) return cuda_fail(e);
     g_ev_start = g_ev_stop = nullptr;
     if ((e = launch_fused(bt, G, false, st)) != cudaSuccess) return cuda_fail(e);
@@ -391,9 +428,14 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
       const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
       if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
         return cuda_fail(e);
-      stage_mark(st);
       ++g_launches;
     }
+    if (p.Wb > 0) {
+      if ((e = launch_stream_bulk(bt, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+        return cuda_fail(e);
+      ++g_launches;
+    }
+    if (p.Wb > 0 || p.W > 0) stage_mark(st);
     if (g_ev_stop && (e = cudaEventRecord(g_ev_stop, st)) != cudaSuccess) return cuda_fail(e);
     g_ev_start = g_ev_stop = nullptr;
     if ((e = launch_compact(bt, st)) != cudaSuccess) return cuda_fail(e);
@@ -711,6 +753,18 @@ int mmlttb_set_timing_events(void* start_event, void* stop_event) {
 
 unsigned long long mmlttb_launch_count(void) { return g_launches; }
 
+int mmlttb_set_stream_staging(int enable) {
+  if (enable != 0 && enable != 1) return MMLTTB_EINVAL;
+  g_bulk_on.store(enable);
+  return MMLTTB_OK;
+}
+
+int mmlttb_get_stream_staging(int* enable) {
+  if (!enable) return MMLTTB_EINVAL;
+  *enable = g_bulk_on.load();
+  return MMLTTB_OK;
+}
+
 int mmlttb_set_single_path(int path) {
   if (path < MMLTTB_PATH_AUTO || path > MMLTTB_PATH_FUSED) return MMLTTB_EINVAL;
   g_path_override = path;
@@ -726,6 +780,19 @@ int mmlttb_single_path(int op, int ydtype, int xkind, int64_t n_in, int64_t n_ou
   rc = plan_single(op, ydtype, xkind, n_in, n_out, r_ps, binmode, d, &p);
   if (rc) return rc;
   return single_path(p, d, n_in, ydtype);
+}
+
+int mmlttb_stream_tiles(int op, int ydtype, int xkind, int64_t n_in, int64_t n_out, int32_t r_ps, int binmode,
+                       int64_t* bins_per_tile) {
+  if (!bins_per_tile) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  SinglePlan p;
+  rc = plan_single(op, ydtype, xkind, n_in, n_out, r_ps, binmode, d, &p);
+  if (rc) return rc;
+  *bins_per_tile = p.bulk_bpt;
+  return MMLTTB_OK;
 }
 
 int mmlttb_workspace_status(const void* workspace, int* status, mmlttb_stream stream) {

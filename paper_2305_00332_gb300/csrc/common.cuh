@@ -46,6 +46,39 @@ constexpr int kBinsPerCta = 256;
 // Threads of the streaming MinMax kernel's CTAs.
 constexpr int kStreamThreads = 256;
 constexpr int kStreamWarps = kStreamThreads / 32;
+// Staged stream (k_stream_bulk) for float32 index bins of at most kBulkMaxBinBytes:
+// every warp runs its own pipeline of kBulkStages shared-memory stages, each filled by
+// one cp.async.bulk copy of a tile (whole bins of one series, at most kBulkTileBytes
+// of y, widened to 16-byte boundaries).  CTAs of kBulkWarps warps, as many per SM as
+// fit.  Measured on 1e8 float32 points it matches or passes the register stream for
+// bins of 16 to 128 points and falls behind it above (fewer bins per tile, per-tile
+// costs less amortised), hence the bin limit.
+constexpr int kBulkWarps = 1;
+constexpr int kBulkStages = 2;
+constexpr int64_t kBulkTileBytes = 8192;
+constexpr int kBulkStageBytes = 8192 + 64;
+constexpr int kBulkSmemBytes = kBulkWarps * kBulkStages * (kBulkStageBytes + 8);
+constexpr int64_t kBulkMaxBinBytes = 512;
+constexpr int64_t kBulkBinCost = 64;  // tile cost of a bin beyond its bytes (record, reduction)
+// Bins per tile of the staged stream for a series with nb binned points of elem_bytes
+// in B index bins (0: the register stream).  Bins hold floor(nb/B) or ceil(nb/B)
+// points, so bpt bins of ceil(nb/B) points fit a tile.
+__host__ __device__ inline int64_t bulk_bins_per_tile(int64_t nb, int64_t B, int elem_bytes) {
+  if (B <= 0 || nb <= 0) return 0;
+  const int64_t smax = (nb + B - 1) / B;
+  if (smax * elem_bytes > kBulkMaxBinBytes) return 0;
+  const int64_t bpt = kBulkTileBytes / elem_bytes / smax;
+  return bpt < B ? bpt : B;
+}
+// Lanes per bin of the staged stream: the 32 lanes cover a tile's bpt bins in one round
+// (a lane per bin from 17 bins per tile on, a whole warp for a one-bin tile).  From
+// shared memory a lane reads its share of a bin at no extra latency, so fewer lanes per
+// bin cost fewer per-bin rounds (bounds, group reduction, record store).
+__host__ __device__ inline int bulk_group(int64_t bpt) {
+  int c = 1;
+  while (c < 32 && c < bpt) c <<= 1;
+  return 32 / c;
+}
 
 // Division by a divisor fixed ahead of the kernel (bins, points, work units, warps,
 // buckets).  An integer division costs hundreds of cycles of latency on this part;
@@ -103,6 +136,11 @@ struct SeriesPlan {
   int64_t tab_off;   // first slot of this series in the table-slot space
   int64_t tab_cap;   // slots reserved (positions that may need a table entry)
   int64_t bincta_off; // first compaction CTA of this series (minmax branches)
+  // staged stream (k_stream_bulk), index bins of at most kBulkTileBytes: bins per tile
+  // (0: the register stream), the series' first unit in the launch's tile cost space
+  // and the cost of one of its tiles, and the record slot offset of its bins (bin b's
+  // record at bin_off + b + rec_w)
+  int64_t bulk_bpt, tcost_off, tcost, rec_w;
   int64_t* sel;      // preselected list (capacity 2B+2), NULL for BR_LTTB_ALL
   double* px;        // x of each preselected position as FP64 (BR_MINMAX_LTTB), else NULL
   double* py;        // y of each preselected position as FP64 (BR_MINMAX_LTTB), else NULL
@@ -140,6 +178,10 @@ struct Batch {
   int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
   int32_t zero_status; // the launch clears the status and barrier words first (first kernel of a call)
   int32_t tab_rounds;  // k_tables: rounds of 32 slots per warp (1..kTableRounds)
+  const int64_t* tcost_offs;  // n_series+1 prefix of the staged stream's tile costs (NULL: single)
+  int64_t total_tcost;  // the tile cost space k_stream_bulk's warps split evenly
+  int64_t n_bulk_warps; // warps of k_stream_bulk
+  Div dtcost, dbwarps;  // divisors total_tcost and n_bulk_warps
 };
 
 __host__ __device__ inline void set_bin_steps(SeriesPlan& sp) {
@@ -157,10 +199,13 @@ __host__ __device__ inline void set_bin_steps(SeriesPlan& sp) {
   sp.bin_rs = (int32_t)(s * sp.nb - sp.bin_qs * sp.B);
 }
 
-// Divisors of the stream's warp partition, after total_pos and n_warps are set.
+// Divisors of the streams' warp partitions, after total_pos, n_warps, total_tcost and
+// n_bulk_warps are set.
 __host__ __device__ inline void set_warp_divs(Batch& bt) {
   bt.dtotal = make_div(bt.total_pos);
   bt.dwarps = make_div(bt.n_warps);
+  bt.dtcost = make_div(bt.total_tcost);
+  bt.dbwarps = make_div(bt.n_bulk_warps);
 }
 
 __host__ __device__ inline const SeriesPlan& plan_of(const Batch& bt, int s) {
@@ -359,6 +404,12 @@ __host__ __device__ inline int64_t warp_of(int64_t g, const Div& total, int64_t 
   return part_of(g + 1, total, warps);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Order-preserving integer keys of y values; -0.0 and +0.0 share key 0.
 __device__ __forceinline__ int key32(float v) {
   int s = __float_as_int(v);
@@ -443,6 +494,10 @@ constexpr int kStreamVariants = 3;
 // ymode: 0 any y (dispatch per series), 1 float32 only, 2 float64 only, 3 float32
 // NaN-aware only, 4 float64 NaN-aware only; see stream_ymode.
 cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode, cudaStream_t st);
+// The staged stream over the series with bulk_bpt > 0 (bt.n_bulk_warps warps), and
+// its resident CTAs per SM.
+cudaError_t launch_stream_bulk(const Batch& bt, int ymode, cudaStream_t st);
+int stream_bulk_blocks_per_sm();
 // The stream-kernel y mode for series of y type ydt: the specialised kernel unless the
 // NaN-aware rule applies.
 inline int stream_ymode(int ydt, bool nan_aware) {

@@ -54,7 +54,7 @@ __device__ __forceinline__ int m4_count(int64_t first, int64_t lo, int64_t hi, i
 }
 
 // Resolve bin b of series sp from its records (consecutive slots, one per warp that
-// streamed part of it): lo/hi = the lower and higher of (first argmin, first
+// streamed part of it; one slot for a series of the staged stream): lo/hi = the lower and higher of (first argmin, first
 // argmax), first/last = the bin's first and last point; all -1 for an empty bin.
 __device__ __forceinline__ void resolve_bin(const Batch& bt, const SeriesPlan& sp, int64_t b,
                                             int64_t* lo, int64_t* hi, int64_t* first, int64_t* last) {
@@ -65,6 +65,12 @@ __device__ __forceinline__ void resolve_bin(const Batch& bt, const SeriesPlan& s
   if (sb >= sb1) return;
   *first = sb;
   *last = sb1 - 1;
+  if (sp.bulk_bpt > 0) {  // staged stream: one record per bin
+    const Record r = bt.rec[sp.bin_off + b + sp.rec_w];
+    *lo = r.imin < r.imax ? r.imin : r.imax;
+    *hi = r.imin < r.imax ? r.imax : r.imin;
+    return;
+  }
   const int64_t wf = warp_of(sp.pos_off + muldiv(sb - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
   const int64_t wl = warp_of(sp.pos_off + muldiv(sb1 - 1 - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
   const Record* rb = bt.rec + sp.bin_off + b;

@@ -23,6 +23,7 @@ struct DevInfo {
   int sms = 0;
   int stream_bps[kStreamVariants] = {};  // resident stream CTAs per SM, per variant
   int fused_grid = 0;  // CTAs of the fused single-series kernel (0: unavailable)
+  int bulk_bps = 1;    // resident staged-stream CTAs per SM
   bool ok = false;
 };
 // SM count and kernel occupancies of the current device (cached per device).
@@ -33,6 +34,14 @@ int stream_variant(const DevInfo& d, int ydt);
 int64_t stream_warp_cap(const DevInfo& d);
 // Streaming warps of `variant` for `work` units: every warp gets at least one point.
 int64_t stream_warps(const DevInfo& d, int variant, int64_t work);
+// Warps of the staged stream for `tiles` tiles: one wave of resident CTAs at most.
+int64_t bulk_warps(const DevInfo& d, int64_t tiles);
+// Record slot offset of a staged series at pos_off of a register work space of
+// `total` units split over W warps: the slots of its bins lie after those of every
+// register-streamed series before it and before those of every one after it.
+int64_t bulk_rec_w(int64_t pos_off, int64_t total, int64_t W);
+// Whether the staged stream is enabled for new plans (mmlttb_set_stream_staging).
+bool bulk_enabled();
 
 // Failure-detection probes (a bounded wait that nothing satisfies; see mmlttb_diag.h).
 cudaError_t launch_sync_probe(const Batch& bt, cudaStream_t st);     // fused.cu grid_sync
@@ -54,6 +63,7 @@ struct BatchImpl {
   int64_t n = 0;
   int64_t total_pos = 0, total_bins = 0, total_edges = 0, total_slots = 0;
   int64_t Wcap = 0, W = 0;
+  int64_t total_tcost = 0, Wb = 0;  // staged stream: tile cost space and warps
   int variant = 0;
   int ymode = 0;  // stream-kernel y mode (stream_ymode) shared by every binned series, else 0
   bool any_block = false;
@@ -61,10 +71,10 @@ struct BatchImpl {
   int64_t total_bin_ctas = 0;
   size_t off_plans = 0, off_pos = 0, off_edge = 0, off_tab = 0, off_cta = 0, off_m = 0, off_edges = 0,
          off_rec = 0, off_sel = 0, off_px = 0, off_py = 0, off_tabs = 0, off_means = 0,
-         off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, total = kHeader,
+         off_binres = 0, off_ctasum = 0, off_ctaser = 0, off_ctaoff = 0, off_tcost = 0, total = kHeader,
          upload_bytes = 0;
   std::vector<int64_t> sel_off, tab_byte_off, mean_off;
-  char* pinned = nullptr;       // upload image: plans | pos_offs | edge_offs | tab_offs | cta_offs
+  char* pinned = nullptr;  // upload image: plans | pos_offs | edge_offs | tab_offs | cta_offs | tcost_offs
   bool own_pinned = true;       // false: the image lives in a buffer lent by the caller
   const void* bound_ws = nullptr;
   cudaGraph_t graph = nullptr;

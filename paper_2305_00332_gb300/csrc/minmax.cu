@@ -20,6 +20,24 @@ __global__ void __launch_bounds__(kStreamThreads, MINB) k_stream(const __grid_co
   stream_warp<U, kY>(bt, w, threadIdx.x & 31);
 }
 
+// The staged stream: CTAs of kBulkWarps warps, every warp with its own kBulkStages
+// shared-memory stages and mbarriers (dynamic shared memory: the stages, then the
+// barriers).
+template <int kY>
+__global__ void __launch_bounds__(kBulkWarps * 32) k_stream_bulk(const __grid_constant__ Batch bt) {
+  extern __shared__ __align__(128) unsigned char s_bulk[];
+  pdl_wait();
+  pdl_trigger();
+  if (bt.zero_status && blockIdx.x == 0 && threadIdx.x == 0) zero_header(bt);
+  const int wid = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kBulkWarps + wid;
+  if (w >= bt.n_bulk_warps) return;
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(s_bulk);
+  const uint32_t sbase = s0 + (uint32_t)(wid * kBulkStages * kBulkStageBytes);
+  const uint32_t bbase = s0 + (uint32_t)(kBulkWarps * kBulkStages * kBulkStageBytes + wid * kBulkStages * 8);
+  bulk_warp<kY>(bt, w, threadIdx.x & 31, sbase, bbase);
+}
+
 __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
@@ -97,6 +115,45 @@ cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode,
     case kYF32Nan: return launch_stream_y<kYF32Nan>(bt, g, b, variant, st);
     case kYF64Nan: return launch_stream_y<kYF64Nan>(bt, g, b, variant, st);
     default: return launch_stream_y<kYAny>(bt, g, b, variant, st);
+  }
+}
+
+template <int kY>
+static cudaError_t launch_bulk_y(const Batch& bt, cudaStream_t st) {
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    e = cudaFuncSetAttribute(k_stream_bulk<kY>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmemBytes);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
+  }
+  const int64_t grid = (bt.n_bulk_warps + kBulkWarps - 1) / kBulkWarps;
+  return launch_pdl(k_stream_bulk<kY>, dim3((unsigned)grid), dim3(kBulkWarps * 32), kBulkSmemBytes, st, bt);
+}
+
+int stream_bulk_blocks_per_sm() {
+  const void* ks[3] = {(const void*)k_stream_bulk<kYAny>, (const void*)k_stream_bulk<kYF32>,
+                       (const void*)k_stream_bulk<kYF32Nan>};
+  int b0 = 0;
+  for (int i = 0; i < 3; ++i) {  // the smallest occupancy of the y modes
+    int bps = 0;
+    if (cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmemBytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, ks[i], kBulkWarps * 32, kBulkSmemBytes) != cudaSuccess)
+      return 1;
+    if (i == 0 || bps < b0) b0 = bps;
+  }
+  return b0 > 0 ? b0 : 1;
+}
+
+cudaError_t launch_stream_bulk(const Batch& bt, int ymode, cudaStream_t st) {
+  if (bt.n_bulk_warps <= 0) return cudaSuccess;
+  switch (ymode) {  // staged series hold float32 y
+    case kYF32: return launch_bulk_y<kYF32>(bt, st);
+    case kYF32Nan: return launch_bulk_y<kYF32Nan>(bt, st);
+    default: return launch_bulk_y<kYAny>(bt, st);
   }
 }
 

@@ -31,6 +31,34 @@ __device__ __forceinline__ uint4 ld_stream4u(const void* p) {
   return v;
 }
 
+// Where a segment routine reads y from: straight from global memory (16-byte
+// streaming loads), or from a window of y staged in shared memory.  Both take the
+// global address of a 16-byte aligned vector of y.
+struct GlobalSrc {
+  __device__ __forceinline__ float4 ld4(uintptr_t a) const { return ld_stream4((const float4*)a); }
+  __device__ __forceinline__ uint4 ld4u(uintptr_t a) const { return ld_stream4u((const void*)a); }
+};
+// A copy of global bytes [g0, g0 + size) at shared address s0 (g0 and s0 16-byte
+// aligned); only vectors inside the copy are read.
+struct SharedSrc {
+  uintptr_t g0;
+  uint32_t s0;
+  __device__ __forceinline__ float4 ld4(uintptr_t a) const {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(s0 + (uint32_t)(a - g0)));
+    return v;
+  }
+  __device__ __forceinline__ uint4 ld4u(uintptr_t a) const {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(s0 + (uint32_t)(a - g0)));
+    return v;
+  }
+};
+
 // NaN-propagating float min/max (a NaN operand makes the result NaN).
 __device__ __forceinline__ float fmin_nan(float a, float b) {
   float r;
@@ -155,8 +183,8 @@ __device__ __forceinline__ unsigned group_min_u32(unsigned v, int G) {
 // kNanAware: NaN-aware mode (R18): a bin holding a NaN reports its first NaN as both
 // extremes; its record carries the keys LLONG_MIN / LLONG_MAX, which no value has,
 // so merging records keeps the first NaN of the bin.
-template <int kUnroll, bool kNanAware>
-__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G) {
+template <int kUnroll, bool kNanAware, class Src = GlobalSrc>
+__device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, int G, const Src& src = Src()) {
   const uint32_t len = (uint32_t)(hi - lo);
   const float inf = __int_as_float(0x7f800000);
   // Empty state: only strictly smaller (larger) values are recorded, so a lane that
@@ -167,7 +195,6 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
   const uintptr_t ybase = (uintptr_t)y;
   const uintptr_t a0 = (ybase + (uintptr_t)lo * 4u) & ~(uintptr_t)15;
   const int32_t rel0 = (int32_t)((int64_t)(a0 - ybase) / 4 - lo);  // offset of vector 0's first element: -3..0
-  const float4* vp = (const float4*)a0;
   // vectors 0..nvec-1 cover the piece; those in [vf, vl) lie wholly inside it, the
   // others (the first when the piece starts mid-vector, the last when it ends
   // mid-vector) are masked
@@ -185,12 +212,12 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
       if (e[k] > mx) { mx = e[k]; omx = (uint32_t)(r + k); }
     }
   };
-  if (gl == 0 && vf == 1 && nvec > 0) masked(ld_stream4(vp), rel0);  // the lowest offsets first
+  if (gl == 0 && vf == 1 && nvec > 0) masked(src.ld4(a0), rel0);  // the lowest offsets first
   for (int32_t v = vf + gl; v < vl; v += G * kUnroll) {
     float4 buf[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; u++)
-      if (v + G * u < vl) buf[u] = ld_stream4(vp + (v + G * u));
+      if (v + G * u < vl) buf[u] = src.ld4(a0 + (uintptr_t)(v + G * u) * 16u);
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
       if (v + G * u >= vl) break;
@@ -219,7 +246,7 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
       }
     }
   }
-  if (gl == 0 && nvec - 1 >= vl && nvec - 1 >= vf) masked(ld_stream4(vp + (nvec - 1)), rel0 + 4 * (nvec - 1));
+  if (gl == 0 && nvec - 1 >= vl && nvec - 1 >= vf) masked(src.ld4(a0 + (uintptr_t)(nvec - 1) * 16u), rel0 + 4 * (nvec - 1));
   int wmn = key32(mn), wmx = key32(mx);
   unsigned wo = omn, wx = omx;
   group_arg32(wmn, wo, wmx, wx, G);
@@ -243,8 +270,8 @@ __device__ Record segment_f32(const float* y, int64_t lo, int64_t hi, int gl, in
 // loop issues no FP64 instruction (FP64 is a narrow pipe on this part): a float
 // compare of the high-word proxies rules out almost every element, and the rest
 // are compared exactly through order-preserving int64 keys.
-template <int kUnroll, bool kNanAware>
-__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G) {
+template <int kUnroll, bool kNanAware, class Src = GlobalSrc>
+__device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, int G, const Src& src = Src()) {
   const uint32_t len = (uint32_t)(hi - lo);
   // Empty state: keys beyond every double's key and NaN proxies, so the first
   // element a lane sees takes the exact path and is recorded.
@@ -283,14 +310,14 @@ __device__ Record segment_f64(const double* y, int64_t lo, int64_t hi, int gl, i
   };
   auto masked = [&](int32_t vi) {
     const int32_t r = rel0 + 2 * vi;
-    update(ld_stream4u((const void*)(a0 + (uintptr_t)vi * 16u)), r, (uint32_t)r < len, (uint32_t)(r + 1) < len);
+    update(src.ld4u(a0 + (uintptr_t)vi * 16u), r, (uint32_t)r < len, (uint32_t)(r + 1) < len);
   };
   if (gl == 0 && vf == 1 && nvec > 0) masked(0);  // the lowest offsets first
   for (int32_t v = vf + gl; v < vl; v += G * kUnroll) {
     uint4 buf[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; u++)
-      if (v + G * u < vl) buf[u] = ld_stream4u((const void*)(a0 + (uintptr_t)(v + G * u) * 16u));
+      if (v + G * u < vl) buf[u] = src.ld4u(a0 + (uintptr_t)(v + G * u) * 16u);
 #pragma unroll
     for (int u = 0; u < kUnroll; u++) {
       if (v + G * u >= vl) break;
@@ -433,6 +460,343 @@ __device__ void stream_warp(const Batch& bt, int64_t w, int lane) {
       g = seg_end;
     }
     ++s;
+  }
+}
+
+// ---- staged stream (k_stream_bulk) ----
+// mbarrier and bulk-copy primitives (shared addresses of this CTA).
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, uintptr_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Test for the completion of phase `parity`; the warp may be suspended (without
+// issuing) until it completes or about `hint_ns` pass.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity, unsigned hint_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of a barrier to complete, for at most 2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity, 20000u)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+// The bins, y window and copy of tile t of a staged series: bins [b0, b1), points
+// [e0, e1), and the 16-byte aligned global bytes [g0, g0 + bytes) holding them (every
+// 16-byte vector of it holds a point of the series, as with the register stream's
+// vector loads).
+struct TileWin {
+  int64_t b0, b1, e0, e1;
+  uintptr_t g0;
+  uint32_t bytes;
+};
+__device__ __forceinline__ TileWin tile_window(const SeriesPlan& sp, int64_t t) {
+  TileWin w;
+  w.b0 = t * sp.bulk_bpt;
+  w.b1 = w.b0 + sp.bulk_bpt < sp.B ? w.b0 + sp.bulk_bpt : sp.B;
+  const int64_t e0 = sp.p0 + muldiv(w.b0, sp.nb, sp.dB);
+  const int64_t e1 = w.b1 >= sp.B ? sp.p0 + sp.nb : sp.p0 + muldiv(w.b1, sp.nb, sp.dB);
+  w.e0 = e0;
+  w.e1 = e1;
+  const uintptr_t es = sp.ydt == MMLTTB_F32 ? 4u : 8u, y = (uintptr_t)sp.y;
+  w.g0 = (y + (uintptr_t)e0 * es) & ~(uintptr_t)15;
+  const uintptr_t g1 = (y + (uintptr_t)e1 * es + 15u) & ~(uintptr_t)15;
+  w.bytes = e1 > e0 ? (uint32_t)(g1 - w.g0) : 0u;
+  return w;
+}
+
+// The tiles a warp takes, in order: those whose first unit lies in the warp's range
+// [c0, c1) of the tile cost space (series s holds units [tcost_off, tcost_off +
+// tiles * tcost)).
+struct TileCursor {
+  int s;
+  int64_t t, t_end, c0, c1;
+  bool done;
+  __device__ void span(const Batch& bt) {  // the tiles of series s in [c0, c1)
+    const SeriesPlan& sp = plan_of(bt, s);
+    t = t_end = 0;
+    if (sp.bulk_bpt <= 0 || sp.tcost <= 0) return;
+    const int64_t nt = (sp.B + sp.bulk_bpt - 1) / sp.bulk_bpt;
+    const int64_t a = c0 - sp.tcost_off, b = c1 - sp.tcost_off;
+    t = a <= 0 ? 0 : (a + sp.tcost - 1) / sp.tcost;
+    t_end = b <= 0 ? 0 : (b + sp.tcost - 1) / sp.tcost;
+    if (t_end > nt) t_end = nt;
+  }
+  __device__ void advance(const Batch& bt) {  // to the next series with a tile in range
+    while (t >= t_end) {
+      if (++s >= bt.n_series || plan_of(bt, s).tcost_off >= c1) {
+        done = true;
+        return;
+      }
+      span(bt);
+    }
+  }
+  __device__ void init(const Batch& bt, int64_t c0_, int64_t c1_) {
+    c0 = c0_;
+    c1 = c1_;
+    done = c0 >= c1;
+    s = bt.tcost_offs ? upper_index(bt.tcost_offs, bt.n_series, c0) : 0;
+    if (done) return;
+    span(bt);
+    advance(bt);
+  }
+  __device__ void next(const Batch& bt) {
+    ++t;
+    advance(bt);
+  }
+};
+
+// Partial MinMax state of a piece of a bin (float32): the smallest and largest value
+// recorded and their first offsets in the tile (kNone: nothing recorded; as in the
+// register stream only values below +inf / above -inf are recorded, so NaN never is),
+// and the first NaN (NaN-aware rule).
+constexpr uint32_t kNone = 0xffffffffu;
+struct Part {
+  float mn, mx;
+  uint32_t imn, imx, inan;
+};
+__device__ __forceinline__ void part_reset(Part& c) {
+  c.mn = __int_as_float(0x7f800000);
+  c.mx = -c.mn;
+  c.imn = c.imx = c.inan = kNone;
+}
+// a and b cover disjoint pieces of one bin: the first occurrence over both
+__device__ __forceinline__ void part_merge(Part& a, const Part& b) {
+  if (b.imn != kNone && (a.imn == kNone || b.mn < a.mn || (b.mn == a.mn && b.imn < a.imn))) {
+    a.mn = b.mn;
+    a.imn = b.imn;
+  }
+  if (b.imx != kNone && (a.imx == kNone || b.mx > a.mx || (b.mx == a.mx && b.imx < a.imx))) {
+    a.mx = b.mx;
+    a.imx = b.imx;
+  }
+  a.inan = b.inan < a.inan ? b.inan : a.inan;
+}
+__device__ __forceinline__ Part part_shfl_down(const Part& c, int d) {
+  Part r;
+  r.mn = __shfl_down_sync(kFull, c.mn, d);
+  r.mx = __shfl_down_sync(kFull, c.mx, d);
+  r.imn = __shfl_down_sync(kFull, c.imn, d);
+  r.imx = __shfl_down_sync(kFull, c.imx, d);
+  r.inan = __shfl_down_sync(kFull, c.inan, d);
+  return r;
+}
+template <bool kNan>
+__device__ __forceinline__ void part_add(Part& c, float v, uint32_t off) {
+  if (kNan && c.inan == kNone && v != v) c.inan = off;
+  if (v < c.mn) {
+    c.mn = v;
+    c.imn = off;
+  }
+  if (v > c.mx) {
+    c.mx = v;
+    c.imx = off;
+  }
+}
+// four consecutive points (offsets off..off+3) of one bin
+template <bool kNan>
+__device__ __forceinline__ void part_add4(Part& c, const float4 b, uint32_t off) {
+  if (kNan && c.inan == kNone && ((b.x != b.x) | (b.y != b.y) | (b.z != b.z) | (b.w != b.w)))
+    c.inan = off + (b.x != b.x ? 0u : b.y != b.y ? 1u : b.z != b.z ? 2u : 3u);
+  const float m4 = fminf(fminf(b.x, b.y), fminf(b.z, b.w));
+  const float x4 = fmaxf(fmaxf(b.x, b.y), fmaxf(b.z, b.w));
+  if (m4 < c.mn) {  // its first occurrence among the four (a NaN equals nothing)
+    c.mn = m4;
+    c.imn = off + (b.x == m4 ? 0u : b.y == m4 ? 1u : b.z == m4 ? 2u : 3u);
+  }
+  if (x4 > c.mx) {
+    c.mx = x4;
+    c.imx = off + (b.x == x4 ? 0u : b.y == x4 ? 1u : b.z == x4 ? 2u : 3u);
+  }
+}
+
+// Record of bin b of a staged series from its complete state (bin first point bstart,
+// tile first point e0): only the indices matter to the compaction.
+template <bool kNan>
+__device__ __forceinline__ void emit_bin(const Batch& bt, const SeriesPlan& sp, int64_t b, const Part& c,
+                                         int64_t bstart, int64_t e0) {
+  Record r;
+  r.kmin = key32(c.mn);
+  r.kmax = key32(c.mx);
+  r.imin = c.imn == kNone ? bstart : e0 + c.imn;
+  r.imax = c.imx == kNone ? bstart : e0 + c.imx;
+  if (kNan && c.inan != kNone) {
+    r.kmin = LLONG_MIN;
+    r.kmax = LLONG_MAX;
+    r.imin = r.imax = e0 + c.inan;
+  }
+  bt.rec[sp.bin_off + b + sp.rec_w] = r;
+}
+
+// Bounds of index bin b: its first point, and the first point after it.
+__device__ __forceinline__ int64_t ibin_start(const SeriesPlan& sp, int64_t b) {
+  return sp.p0 + muldiv(b, sp.nb, sp.dB);
+}
+__device__ __forceinline__ int64_t ibin_end(const SeriesPlan& sp, int64_t b) {
+  return b + 1 >= sp.B ? sp.p0 + sp.nb : sp.p0 + muldiv(b + 1, sp.nb, sp.dB);
+}
+
+// The bins of one staged float32 tile, read from shared memory: groups of G lanes
+// (sp.group) take 32/G bins per round, bin bounds stepped from the series' constants
+// (no division per bin).  Within a bin the G lanes read its whole 16-byte vectors in
+// turn (consecutive lanes, consecutive vectors) with no range test; the group's first
+// lane also takes the partial vectors at the bin's two ends, masked.  A butterfly over the
+// group joins the lanes' Parts and the first lane writes the bin's record.
+template <bool kNan>
+__device__ void bulk_tile_f32(const Batch& bt, const SeriesPlan& sp, const TileWin& tw, uint32_t sdst, int lane) {
+  const int G = sp.group, ngroups = 32 / G;
+  const int grp = lane / G, gl = lane - grp * G;
+  const int64_t e0 = tw.e0;
+  const int64_t pbase = ((int64_t)tw.g0 - (int64_t)(uintptr_t)sp.y) / 4;  // point of the window's first float
+  auto ld = [&](int64_t k) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(sdst + 16u * (uint32_t)k));
+    return v;
+  };
+  // bin mb = b0 + grp: lo = p0 + floor(mb*nb/B), rem = mb*nb mod B; later bins by
+  // steps of one bin (q1, r1) and of 32/G bins (qs, rs)
+  const int64_t mb0 = tw.b0 + grp;
+  int64_t lo = ibin_start(sp, mb0);
+  uint64_t rem = (uint64_t)mb0 * (uint64_t)sp.nb - (uint64_t)(lo - sp.p0) * (uint64_t)sp.B;
+  const uint64_t Bu = (uint64_t)sp.B, r1 = (uint64_t)sp.bin_r1, rs = (uint64_t)sp.bin_rs;
+  for (int64_t bb = tw.b0; bb < tw.b1; bb += ngroups) {
+    const int64_t mb = bb + grp;
+    const int64_t hi = lo + sp.bin_q1 + (rem + r1 >= Bu ? 1 : 0);  // start of bin mb + 1
+    Part c;
+    part_reset(c);
+    const bool active = mb < tw.b1 && lo < hi;
+    if (active) {
+      const int64_t ka = (lo - pbase) >> 2, kb = (hi - 1 - pbase) >> 2;  // first and last vector
+      const int64_t kf = (lo - pbase) & 3 ? ka + 1 : ka;                 // whole vectors [kf, kl)
+      const int64_t kl = (hi - pbase) & 3 ? kb : kb + 1;
+      // each lane takes its points in increasing order: the partial first vector,
+      // the whole vectors, the partial last vector
+      auto masked = [&](int64_t k) {
+        const float4 v = ld(k);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t p = pbase + 4 * k + j;
+          if (p >= lo && p < hi) part_add<kNan>(c, e[j], (uint32_t)(p - e0));
+        }
+      };
+      if (gl == 0 && kf != ka) masked(ka);
+      int64_t k = kf + gl;
+      for (; k + 3 * G < kl; k += 4 * G) {  // four reads in flight, then their reductions
+        const float4 a0 = ld(k), a1 = ld(k + G), a2 = ld(k + 2 * G), a3 = ld(k + 3 * G);
+        const uint32_t o = (uint32_t)(pbase + 4 * k - e0), og = 4u * (uint32_t)G;
+        part_add4<kNan>(c, a0, o);
+        part_add4<kNan>(c, a1, o + og);
+        part_add4<kNan>(c, a2, o + 2 * og);
+        part_add4<kNan>(c, a3, o + 3 * og);
+      }
+      for (; k < kl; k += G) part_add4<kNan>(c, ld(k), (uint32_t)(pbase + 4 * k - e0));
+      if (gl == 0 && kl == kb && !(kf != ka && kb == ka)) masked(kb);
+    }
+    for (int d = 1; d < G; d <<= 1) {  // every lane takes part
+      Part o;
+      o.mn = __shfl_xor_sync(kFull, c.mn, d);
+      o.mx = __shfl_xor_sync(kFull, c.mx, d);
+      o.imn = __shfl_xor_sync(kFull, c.imn, d);
+      o.imx = __shfl_xor_sync(kFull, c.imx, d);
+      o.inan = __shfl_xor_sync(kFull, c.inan, d);
+      part_merge(c, o);
+    }
+    if (active && gl == 0) emit_bin<kNan>(bt, sp, mb, c, lo, e0);
+    // the next round: bin mb + 32/G
+    lo += sp.bin_qs;
+    rem += rs;
+    if (rem >= Bu) {
+      rem -= Bu;
+      lo += 1;
+    }
+  }
+}
+
+// Staged-stream warp w: its tiles, each copied by one cp.async.bulk (lane 0 issues;
+// an mbarrier per stage counts the bytes) into the next of its kBulkStages stages
+// while the lanes reduce an earlier one, so that kBulkStages - 1 copies are in flight.
+// Every wait is bounded: on a timeout the warp sets status bit 1, waits (bounded) for
+// its copies still in flight and returns.
+template <int kY>
+__device__ void bulk_warp(const Batch& bt, int64_t w, int lane, uint32_t sbase, uint32_t bbase) {
+  TileCursor cons;
+  cons.init(bt, warp_begin(w, bt.total_tcost, bt.dbwarps), warp_begin(w + 1, bt.total_tcost, bt.dbwarps));
+  if (cons.done) return;
+  if (lane == 0) {
+    for (int i = 0; i < kBulkStages; ++i) mbar_init(bbase + 8u * i, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  TileCursor prod = cons;
+  auto issue = [&](int st) {
+    if (lane == 0) {
+      const TileWin pw = tile_window(plan_of(bt, prod.s), prod.t);
+      const uint32_t bar = bbase + 8u * st;
+      mbar_arrive_tx(bar, pw.bytes);
+      if (pw.bytes) bulk_copy_g2s(sbase + (uint32_t)st * kBulkStageBytes, pw.g0, pw.bytes, bar);
+    }
+    prod.next(bt);
+  };
+  int inflight = 0;
+  for (int i = 0; i < kBulkStages && !prod.done; ++i, ++inflight) issue(i);
+  int st = 0;
+  unsigned phase = 0;
+  while (!cons.done) {
+    if (!mbar_wait_bounded(bbase + 8u * st, phase)) {
+      if (lane == 0) atomicOr(bt.status, 1u);
+      for (int i = 1; i < inflight; ++i) {  // the copies issued after this stage
+        const int s2 = (st + i) % kBulkStages;
+        mbar_wait_bounded(bbase + 8u * s2, phase ^ (s2 < st ? 1u : 0u));
+      }
+      return;
+    }
+    const SeriesPlan& sp = plan_of(bt, cons.s);
+    const TileWin tw = tile_window(sp, cons.t);
+    const bool nan = kY == kYF32Nan || (kY == kYAny && sp.nan_aware);
+    if (nan)
+      bulk_tile_f32<true>(bt, sp, tw, sbase + (uint32_t)st * kBulkStageBytes, lane);
+    else
+      bulk_tile_f32<false>(bt, sp, tw, sbase + (uint32_t)st * kBulkStageBytes, lane);
+    cons.next(bt);
+    __syncwarp();
+    --inflight;
+    if (!prod.done) {
+      if (lane == 0) fence_proxy_async();  // the lanes' reads of this stage before its refill
+      issue(st);
+      ++inflight;
+    }
+    if (++st == kBulkStages) {
+      st = 0;
+      phase ^= 1u;
+    }
   }
 }
 
