@@ -59,8 +59,12 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the plain-LTTB, batched and serving sub-records")
     ap.add_argument("--workload", default="1e9-xwidth",
-                    choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving", "visual"],
+                    choices=["1e9-xwidth", "1e6", "1e8-vs-lttb", "batched-4096", "serving", "visual", "bins"],
                     help="the headline (default) or one of the other measured workloads")
+    ap.add_argument("--series", type=int, default=4096,
+                    help="batched-4096: run the first N of its series (a smaller case for profiling)")
+    ap.add_argument("--bin-points", type=int, default=0,
+                    help="bins: one bin size in points (default: the sweep)")
     return ap.parse_args()
 
 

@@ -10,6 +10,8 @@
   serving       64 resident series of 1e8 float32 points; Poisson zoom-window requests
                 (width log-uniform in [1e4, 1e8], n_out in U{500..4000}, r_ps=4) at several
                 rates; continuous-batching server vs one request per launch; p50/p99.
+  bins          MinMax stream rate by index-bin size (16 to 25 000 points) on 1e8 float32
+                walk points, register stream against the staged (cp.async.bulk) stream.
   visual        line charts on an 800 x 250 canvas: rasteriser throughput on the chart of
                 all points of a 1e7 float32 walk + sines + spikes; and for a 2e5-point
                 template of the same kind (the reference-image size of the paper's figure)
@@ -195,16 +197,19 @@ def run_1e8(args, mm):
 BATCH_SEED = 1000
 
 
-def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps=3):
+def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps=3, n_series=4096):
     """4096 float32 walks, lengths round(10^U(3,7)), n_out U{200..4000}, r_ps = 4: one
-    batched launch sequence replayed as a CUDA graph, against 4096 single calls."""
+    batched launch sequence replayed as a CUDA graph, against 4096 single calls.  With
+    n_series < 4096, the first n_series of those series (a smaller case of the same
+    mix, for profiling)."""
     lens, nouts = synth.batch_shapes(4096, seed=0)
+    lens, nouts = lens[:n_series], nouts[:n_series]
     t = time.time()
     ys_h = synth.random_walks(lens, BATCH_SEED)
     gen = time.time() - t
     ys = [torch.from_numpy(v).cuda() for v in ys_h]
     total = int(lens.sum())
-    sample = sorted(set(np.random.default_rng(1).choice(4096, 48, replace=False).tolist())
+    sample = sorted(set(np.random.default_rng(1).choice(n_series, min(48, n_series), replace=False).tolist())
                     | set(np.argsort(lens)[-4:].tolist()))
     ys_h = {i: ys_h[i] for i in sample}  # the host copies the oracle sample needs
     b = mm.Batch([{"y": y, "n_out": int(k), "r_ps": 4} for y, k in zip(ys, nouts)])
@@ -252,13 +257,14 @@ def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps
     clk.stop()
     res = b.results()
     same = all(torch.equal(res[i], outs[i][: res[i].numel()]) and res[i].numel() == outs[i].numel()
-               for i in range(4096))
+               for i in range(n_series))
     g = _med(per)
     v = ctypes.c_int(-1)
     mm.lib.mmlttb_get_stream_variant(mm.F32, ctypes.byref(v))
     unroll, min_blocks = mm.stream_variants()[v.value] if v.value >= 0 else (None, None)
     variant = {"variant": v.value, "loads_in_flight_per_lane": unroll, "ctas_per_sm": min_blocks}
-    rec = {"workload": "4096 float32 walks, lengths round(10^U(3,7)), n_out U{200..4000}, r_ps=4, implicit x",
+    what = "4096 float32 walks" if n_series == 4096 else f"the first {n_series} of the 4096 float32 walks"
+    rec = {"workload": what + ", lengths round(10^U(3,7)), n_out U{200..4000}, r_ps=4, implicit x",
            "total_points": total, "steps": steps, "warmup": warmup, "dtype": "f32",
            "graph_ms": g, "graph_ms_mean": sum(per) / len(per), "gpts_per_s": total / (g * 1e-3) / 1e9,
            "singles_ms": _med(sper), "singles_gpts_per_s": total / (_med(sper) * 1e-3) / 1e9,
@@ -294,9 +300,53 @@ def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps
 
 
 def run_batched(args, mm):
-    rec = record_batched(mm, max(5, args.steps // 10), max(3, args.warmup))
-    _line("batched MinMaxLTTB throughput, 4096 series (Gpts/s)", rec["gpts_per_s"], "Gpts/s", True,
+    rec = record_batched(mm, max(5, args.steps // 10), max(3, args.warmup), n_series=args.series)
+    _line(f"batched MinMaxLTTB throughput, {args.series} series (Gpts/s)", rec["gpts_per_s"], "Gpts/s", True,
           {"workload": rec["workload"], "total_points": rec["total_points"]}, rec, args)
+
+
+def run_bins(args, mm):
+    """MinMax stream rate by index-bin size on 1e8 float32 walk points (preselection,
+    r_ps = 2, n_out = points per bin / (n - 2)): the register stream and the staged
+    (cp.async.bulk) stream, CUDA events around the stream kernel, the same indices."""
+    n = 100_000_000
+    y = torch.from_numpy(synth.random_walk(n, seed=3, dtype=np.float32)).cuda()
+    sizes = [args.bin_points] if args.bin_points else [16, 64, 125, 256, 1024, 4096, 25000]
+    rows = []
+    clk = _clocks("0")
+    t0 = time.time()
+    for S in sizes:
+        n_out = max(3, int((n - 2) / S))
+        row = {"points_per_bin": S}
+        outs = {}
+        for staged in (False, True):
+            mm.set_stream_staging(staged)
+            tiles = mm.stream_tiles(mm.OP_PRESELECT, mm.F32, mm.X_IMPLICIT, n, n_out, 2)
+            if staged and tiles == 0:
+                row["staged_gbs"] = None  # bins too large for the staged stream
+                continue
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            b.record()
+            ts = []
+            for r in range(max(3, args.warmup) + max(3, args.steps)):
+                mm.set_timing_events(a, b)
+                outs[staged] = mm.minmax_preselect(y, n_out, 2)
+                torch.cuda.synchronize()
+                if r >= max(3, args.warmup):
+                    ts.append(a.elapsed_time(b))
+            row["staged_gbs" if staged else "register_gbs"] = 4 * (n - 2) / (_med(ts) * 1e-3) / 1e9
+        mm.set_stream_staging(False)
+        row["same_indices"] = len(outs) < 2 or bool(torch.equal(outs[False], outs[True]))
+        rows.append(row)
+    t1 = time.time()
+    clk.stop()
+    peak, peak_src = _peak_gbs()
+    best = max(max(r["register_gbs"], r["staged_gbs"] or 0) for r in rows)
+    _line("MinMax stream rate by bin size, 1e8 float32 points (GB/s)", best, "GB/s", True,
+          {"workload": "1e8 float32 walk, MinMax preselection r_ps=2, index bins of the given points"},
+          {"rows": rows, "peak": peak, "peak_source": peak_src, "dtype": "f32",
+           "l2": "no flush: 400 MB of y per step exceed L2 (129 MB)", "clocks": clk.summary(t0, t1)}, args)
 
 
 SERVE_SEED = 5000
@@ -466,4 +516,4 @@ def run(args):
     import paper_2305_00332_gb300 as mm
     torch.cuda.set_device(0)
     {"1e6": run_1e6, "1e8-vs-lttb": run_1e8, "batched-4096": run_batched, "serving": run_serving,
-     "visual": run_visual}[args.workload](args, mm)
+     "visual": run_visual, "bins": run_bins}[args.workload](args, mm)
