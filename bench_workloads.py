@@ -213,6 +213,7 @@ def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps
                     | set(np.argsort(lens)[-4:].tolist()))
     ys_h = {i: ys_h[i] for i in sample}  # the host copies the oracle sample needs
     b = mm.Batch([{"y": y, "n_out": int(k), "r_ps": 4} for y, k in zip(ys, nouts)])
+    tuning = b.tuning()  # the tuple the batch was planned with
     # kernel breakdown of one uncaptured run (stage events at fixed points)
     names = ["upload", "edges", "stream", "compaction", "tables", "chain", "block"]
     stage = {k: [] for k in names[1:]}
@@ -259,10 +260,9 @@ def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps
     same = all(torch.equal(res[i], outs[i][: res[i].numel()]) and res[i].numel() == outs[i].numel()
                for i in range(n_series))
     g = _med(per)
-    v = ctypes.c_int(-1)
-    mm.lib.mmlttb_get_stream_variant(mm.F32, ctypes.byref(v))
-    unroll, min_blocks = mm.stream_variants()[v.value] if v.value >= 0 else (None, None)
-    variant = {"variant": v.value, "loads_in_flight_per_lane": unroll, "ctas_per_sm": min_blocks}
+    unroll, min_blocks = mm.stream_variants()[tuning["variant"]]
+    variant = {"tuning": tuning, "loads_in_flight_per_lane": unroll, "ctas_per_sm": min_blocks,
+               "threads_per_cta": mm.stream_variant_threads(tuning["variant"])}
     what = "4096 float32 walks" if n_series == 4096 else f"the first {n_series} of the 4096 float32 walks"
     rec = {"workload": what + ", lengths round(10^U(3,7)), n_out U{200..4000}, r_ps=4, implicit x",
            "total_points": total, "steps": steps, "warmup": warmup, "dtype": "f32",

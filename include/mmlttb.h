@@ -366,22 +366,50 @@ int mmlttb_set_timing_events(void *start_event, void *stop_event);
 int mmlttb_set_stage_events(void *const *events, int count);
 
 /*
- * Autotuning of the streaming MinMax kernel (the HBM-bound step of the MinMax
- * preselection, Sec. 3; tuning has no counterpart in the paper).  The library
- * carries several compiled variants of it, differing in 16-byte loads in flight
- * per lane and in resident CTAs per SM (see mmlttb_stream_variant_info); the
- * number of lanes that share a bin is chosen per series from its mean bin size.
- * mmlttb_autotune times every variant on MinMax preselection of the caller's y
- * (device, n_in values; index bins, n_out and r_ps as given; out_idx and the
- * workspace as for mmlttb_minmax_preselect), blocking, and makes the fastest one
- * the variant for that y type on the current device (*best_variant, *best_ms =
- * its median kernel time).  The choice lasts for the process; get/set let a
- * caller persist and restore it.
+ * Autotuning (no counterpart in the paper, which fixes results, not launches; every
+ * tuning returns the same indices).  A tuning is the tuple
+ *   variant      the streaming MinMax kernel: 16-byte loads in flight per lane, resident
+ *                CTAs per SM and threads per CTA (mmlttb_stream_variant_info,
+ *                mmlttb_stream_variant_threads), 0 .. MMLTTB_STREAM_VARIANTS - 1;
+ *   group_shift  lanes per index bin of the register stream: the size-based choice
+ *                doubled (+1), kept (0) or halved (-1), within 1 .. 32;
+ *   tab_rounds   rounds of 32 table slots per warp of k_tables, 1 .. 7 (0: chosen from
+ *                the slot count).
+ * Tunings are kept per process under a key: the current device, the y type, the x
+ * kind, the bin mode and the size class (the decimal digits of n_in less one, at most
+ * 12).  Single-series calls use the tuning of their key; a batch, the one of the key
+ * that holds most of its binned points, its size class from its total points
+ * (mmlttb_batch_tuning reports it).  Keys never set use the default {0 or the variant
+ * set for the y type by mmlttb_set_stream_variant, 0, 0}.
+ * mmlttb_autotune_tuple times, blocking, every variant x group_shift on MinMax
+ * preselection of the caller's series (device y and, for int64/float64 x, x; n_in,
+ * n_out, r_ps, bin mode as given; workspace as for mmlttb_minmaxlttb, which must also
+ * fit out_idx's needs), then tab_rounds in {0, 2, 4, 7} on MinMaxLTTB of it, stores
+ * the fastest tuple under the series' key and returns it (*best_ms: the median stream
+ * kernel time of the chosen variant).  mmlttb_autotune is the older entry point: it
+ * tunes the variant alone for implicit x and index bins and also makes it the
+ * variant of that y type.  set/get let a caller persist and restore tunings.
+ * MMLTTB_EINVAL for a NULL pointer, an unknown type or kind, or a field out of range.
  */
+#define MMLTTB_STREAM_VARIANTS 6
+typedef struct mmlttb_tuning {
+  int32_t variant;
+  int32_t group_shift;
+  int32_t tab_rounds;
+  int32_t reserved; /* 0 */
+} mmlttb_tuning;
 int mmlttb_stream_variant_info(int variant, int *unroll, int *min_blocks);
+int mmlttb_stream_variant_threads(int variant, int *threads);
 int mmlttb_autotune(int ydtype, const void *y, int64_t n_in, int64_t n_out, int32_t r_ps,
                     int64_t *out_idx, int64_t out_cap, void *workspace, size_t workspace_bytes,
                     mmlttb_stream stream, int *best_variant, float *best_ms);
+int mmlttb_autotune_tuple(int ydtype, const void *y, int xkind, const void *x, int64_t n_in, int64_t n_out,
+                          int32_t r_ps, int binmode, int64_t *out_idx, int64_t out_cap, void *workspace,
+                          size_t workspace_bytes, mmlttb_stream stream, mmlttb_tuning *best, float *best_ms);
+int mmlttb_set_tuning(int ydtype, int xkind, int binmode, int64_t n_in, const mmlttb_tuning *tuning);
+int mmlttb_get_tuning(int ydtype, int xkind, int binmode, int64_t n_in, mmlttb_tuning *tuning);
+int mmlttb_clear_tunings(void);
+int mmlttb_batch_tuning(mmlttb_batch_t batch, mmlttb_tuning *tuning);
 int mmlttb_get_stream_variant(int ydtype, int *variant);
 int mmlttb_set_stream_variant(int ydtype, int variant);
 

@@ -344,8 +344,91 @@ def autotune(y, n_out=4000, r_ps=4, save=True):
     return v.value, ms.value
 
 
+class Tuning(ctypes.Structure):
+    """mmlttb_tuning: stream-kernel variant, lanes-per-bin shift, k_tables rounds."""
+    _fields_ = [("variant", _i32), ("group_shift", _i32), ("tab_rounds", _i32), ("reserved", _i32)]
+
+    def as_dict(self):
+        return {"variant": self.variant, "group_shift": self.group_shift, "tab_rounds": self.tab_rounds}
+
+
+lib.mmlttb_stream_variant_threads.argtypes = [_int, ctypes.POINTER(_int)]
+lib.mmlttb_set_tuning.argtypes = [_int, _int, _int, _i64, ctypes.POINTER(Tuning)]
+lib.mmlttb_get_tuning.argtypes = [_int, _int, _int, _i64, ctypes.POINTER(Tuning)]
+lib.mmlttb_autotune_tuple.argtypes = [_int, _vp, _int, _vp, _i64, _i64, _i32, _int, _vp, _i64, _vp, _sz, _vp,
+                                      ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
+lib.mmlttb_batch_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]
+
+
+def stream_variant_threads(variant):
+    t = _int(0)
+    _check(lib.mmlttb_stream_variant_threads(variant, ctypes.byref(t)), "mmlttb_stream_variant_threads")
+    return t.value
+
+
+def set_tuning(ydtype, xkind, binmode, n_in, variant, group_shift=0, tab_rounds=0):
+    """Store a tuning for the key (current device, y type, x kind, bin mode, size class
+    of n_in)."""
+    t = Tuning(variant, group_shift, tab_rounds, 0)
+    _check(lib.mmlttb_set_tuning(ydtype, xkind, binmode, n_in, ctypes.byref(t)), "mmlttb_set_tuning")
+
+
+def get_tuning(ydtype, xkind, binmode, n_in):
+    """The tuning calls with this key use (the stored one, else the default)."""
+    t = Tuning()
+    _check(lib.mmlttb_get_tuning(ydtype, xkind, binmode, n_in, ctypes.byref(t)), "mmlttb_get_tuning")
+    return t.as_dict()
+
+
+def clear_tunings():
+    _check(lib.mmlttb_clear_tunings(), "mmlttb_clear_tunings")
+
+
+def _size_class(n):
+    c = 0
+    while n >= 10 and c < 12:
+        n //= 10
+        c += 1
+    return c
+
+
+def autotune_tuple(y, n_out=4000, r_ps=4, x=None, binmode=BINS_INDEX, save=True):
+    """Time every stream variant x lanes-per-bin shift on MinMax preselection of y (and
+    x), then k_tables rounds on MinMaxLTTB of it; store the fastest tuning under the
+    series' key and, with save, in the tuning cache (JSON keyed by device name, y type,
+    x kind, bin mode and size class).  Returns (tuning dict, median stream ms)."""
+    import json
+    _check_inputs(y, x)
+    yd, xk, bm = _ydt(y), _xkind(x), _binmode(binmode)
+    n = y.numel()
+    cap = max(1, min(n, (n_out * r_ps // 2) * 2 + 2))
+    out = torch.empty(cap, dtype=torch.int64, device=y.device)
+    wsb = max(workspace_bytes(OP_PRESELECT, yd, xk, n, n_out, r_ps, bm),
+              workspace_bytes(OP_MINMAXLTTB, yd, xk, n, n_out, r_ps, bm))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=y.device)
+    t, ms = Tuning(), ctypes.c_float(0.0)
+    with torch.cuda.device(y.device):
+        _check(lib.mmlttb_autotune_tuple(yd, y.data_ptr(), xk, x.data_ptr() if x is not None else None, n, n_out,
+                                         r_ps, bm, out.data_ptr(), out.numel(), ws.data_ptr(), ws.numel(),
+                                         _stream(y.device), ctypes.byref(t), ctypes.byref(ms)),
+               "mmlttb_autotune_tuple")
+    if save:
+        path = _tune_cache_path()
+        try:
+            cache = json.load(open(path)) if os.path.exists(path) else {}
+        except (OSError, ValueError):
+            cache = {}
+        key = f"{torch.cuda.get_device_name(y.device)}/tuple/{yd}/{xk}/{bm}/{_size_class(n)}"
+        cache[key] = t.as_dict()
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return t.as_dict(), ms.value
+
+
 def load_tuning(device=None):
-    """Apply the cached stream-kernel choices for `device` (if any were saved)."""
+    """Apply the cached tunings for `device` (if any were saved): stream variants per y
+    type, and tuples per (y type, x kind, bin mode, size class)."""
     import json
     path = _tune_cache_path()
     if not os.path.exists(path):
@@ -360,6 +443,12 @@ def load_tuning(device=None):
             if v is not None:
                 _check(lib.mmlttb_set_stream_variant(yd, int(v)), "mmlttb_set_stream_variant")
                 applied[key] = v
+        for key, t in cache.items():
+            parts = key.split("/")
+            if len(parts) == 6 and parts[0] == name and parts[1] == "tuple":
+                yd, xk, bm, c = (int(q) for q in parts[2:])
+                set_tuning(yd, xk, bm, 10 ** c, t["variant"], t["group_shift"], t["tab_rounds"])
+                applied[key] = t
     return applied
 
 
@@ -598,6 +687,12 @@ class Batch:
     def results(self):
         counts = self.counts.cpu().tolist()
         return [self.out[self.offsets[i]: self.offsets[i] + counts[i]] for i in range(len(counts))]
+
+    def tuning(self):
+        """The tuning the batch was planned with (mmlttb_batch_tuning)."""
+        t = Tuning()
+        _check(lib.mmlttb_batch_tuning(self._h, ctypes.byref(t)), "mmlttb_batch_tuning")
+        return t.as_dict()
 
     def close(self):
         if getattr(self, "_h", None):

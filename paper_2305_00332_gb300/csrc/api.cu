@@ -77,10 +77,56 @@ int stream_variant(const DevInfo& d, int ydt) {
   return g_variant[d.device][ydt].load();
 }
 
+// ---- tunings (mmlttb_tuning), per process under (device, y type, x kind, bin mode,
+// size class)
+constexpr int kSizeClasses = 13;
+std::mutex g_tune_mu;
+bool g_tune_set[64][2][3][2][kSizeClasses];
+mmlttb_tuning g_tune[64][2][3][2][kSizeClasses];
+thread_local const mmlttb_tuning* g_tune_override = nullptr;  // while tuning
+
+int size_class(int64_t n) {
+  int c = 0;
+  while (n >= 10 && c < kSizeClasses - 1) {
+    n /= 10;
+    ++c;
+  }
+  return c;
+}
+
+bool tuning_valid(const mmlttb_tuning& t) {
+  return t.variant >= 0 && t.variant < kStreamVariants && t.group_shift >= -1 && t.group_shift <= 1 &&
+         t.tab_rounds >= 0 && t.tab_rounds <= kTableRoundsMax && t.reserved == 0;
+}
+
+bool tune_key_ok(const DevInfo& d, int ydt, int xk, int binmode) {
+  return d.device >= 0 && d.device < 64 && (ydt == MMLTTB_F32 || ydt == MMLTTB_F64) && xk >= 0 && xk <= 2 &&
+         (binmode == MMLTTB_BINS_INDEX || binmode == MMLTTB_BINS_XWIDTH);
+}
+
+mmlttb_tuning tuning_for(const DevInfo& d, int ydt, int xk, int binmode, int64_t n) {
+  if (g_tune_override) return *g_tune_override;
+  mmlttb_tuning t{stream_variant(d, ydt), 0, 0, 0};
+  binmode &= ~MMLTTB_NAN_AWARE;
+  if (tune_key_ok(d, ydt, xk, binmode)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int c = size_class(n);
+    if (g_tune_set[d.device][ydt][xk][binmode][c]) t = g_tune[d.device][ydt][xk][binmode][c];
+  }
+  if (g_variant_override >= 0) t.variant = g_variant_override;
+  return t;
+}
+
+int shift_group(int G, int shift) {
+  if (shift > 0) return G < 32 ? G << 1 : 32;
+  if (shift < 0) return G > 1 ? G >> 1 : 1;
+  return G;
+}
+
 int64_t stream_warp_cap(const DevInfo& d) {
   int64_t c = 0;
   for (int v = 0; v < kStreamVariants; ++v) {
-    const int64_t w = (int64_t)d.sms * d.stream_bps[v] * kStreamWarps;
+    const int64_t w = (int64_t)d.sms * d.stream_bps[v] * (stream_variant_threads(v) / 32);
     if (w > c) c = w;
   }
   return c;
@@ -88,7 +134,7 @@ int64_t stream_warp_cap(const DevInfo& d) {
 
 int64_t stream_warps(const DevInfo& d, int variant, int64_t work) {
   int64_t W = work / (kBinCostMax + 1);
-  const int64_t cap = (int64_t)d.sms * d.stream_bps[variant] * kStreamWarps;
+  const int64_t cap = (int64_t)d.sms * d.stream_bps[variant] * (stream_variant_threads(variant) / 32);
   if (W > cap) W = cap;
   if (W < 1 && work > 0) W = 1;
   return W;
@@ -119,6 +165,7 @@ struct SinglePlan {
   int group = 32;   // lanes per bin in the stream
   int tab_lgS = 0;  // log2 of the fused tables' slots per bucket
   int variant = 0;  // stream-kernel variant
+  int tab_rounds = 0;  // k_tables rounds per warp (0: from the slot count)
   int64_t bulk_bpt = 0, tcost = 0, tiles = 0, Wb = 0;  // staged stream (bulk_bpt > 0)
   size_t total = kHeader;
 };
@@ -186,7 +233,12 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     p.nb = N;
     // x-width bins can be very uneven: keep whole warps per bin there
     const int eb = ydt == MMLTTB_F32 ? 4 : 8;
-    p.group = binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(N, p.B, eb, N * eb >= kStreamThroughputBytes);
+    const mmlttb_tuning tu = tuning_for(d, ydt, xk, binmode, n);
+    p.variant = tu.variant;
+    p.tab_rounds = tu.tab_rounds;
+    p.group = binmode == MMLTTB_BINS_XWIDTH
+                  ? 32
+                  : shift_group(stream_group(N, p.B, eb, N * eb >= kStreamThroughputBytes), tu.group_shift);
     if (binmode == MMLTTB_BINS_INDEX && ydt == MMLTTB_F32 && N * eb >= kStreamThroughputBytes && bulk_enabled())
       p.bulk_bpt = bulk_bins_per_tile(N, p.B, eb);
     if (p.bulk_bpt > 0) {  // the staged stream: no register-stream work
@@ -197,7 +249,6 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     }
     p.npos = p.bulk_bpt > 0 ? 0 : series_work(N, p.B, p.group);
     p.Wcap = stream_warp_cap(d);
-    p.variant = stream_variant(d, ydt);
     p.W = stream_warps(d, p.variant, p.npos);
     if (p.W > 0 && N / p.W >= (int64_t(1) << 30)) return MMLTTB_EINVAL;  // per-warp span
     if (binmode == MMLTTB_BINS_XWIDTH) {
@@ -340,6 +391,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
   bt.total_pos = p.npos;
   bt.n_warps = p.W;
   bt.tcost_offs = nullptr;
+  bt.tab_rounds_req = p.tab_rounds;
   bt.total_tcost = p.tiles * p.tcost;
   bt.n_bulk_warps = p.Wb;
   set_warp_divs(bt);
@@ -388,8 +440,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     }
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
-      const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
-      if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+      if ((e = launch_stream(bt, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
         return cuda_fail(e);
       ++g_launches;
       bt.zero_status = 0;
@@ -425,8 +476,7 @@ int run_single(int op, const void* y, int ydt, const void* x, int xk, int64_t n,
     }
     if (g_ev_start && (e = cudaEventRecord(g_ev_start, st)) != cudaSuccess) return cuda_fail(e);
     if (p.W > 0) {
-      const int64_t grid = (p.W + kStreamWarps - 1) / kStreamWarps;
-      if ((e = launch_stream(bt, grid, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
+      if ((e = launch_stream(bt, p.variant, stream_ymode(ydt, sp.nan_aware != 0), st)) != cudaSuccess)
         return cuda_fail(e);
       ++g_launches;
     }
@@ -734,6 +784,121 @@ int mmlttb_autotune(int ydtype, const void* y, int64_t n_in, int64_t n_out, int3
   if (d.device >= 0 && d.device < 64) g_variant[d.device][ydtype].store(bv);
   *best_variant = bv;
   if (best_ms) *best_ms = best;
+  return MMLTTB_OK;
+}
+
+int mmlttb_stream_variant_threads(int variant, int* threads) {
+  if (!threads || variant < 0 || variant >= kStreamVariants) return MMLTTB_EINVAL;
+  *threads = stream_variant_threads(variant);
+  return MMLTTB_OK;
+}
+
+int mmlttb_set_tuning(int ydtype, int xkind, int binmode, int64_t n_in, const mmlttb_tuning* tuning) {
+  if (!tuning || !tuning_valid(*tuning)) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  binmode &= ~MMLTTB_NAN_AWARE;
+  if (!tune_key_ok(d, ydtype, xkind, binmode)) return MMLTTB_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int c = size_class(n_in);
+  g_tune[d.device][ydtype][xkind][binmode][c] = *tuning;
+  g_tune_set[d.device][ydtype][xkind][binmode][c] = true;
+  return MMLTTB_OK;
+}
+
+int mmlttb_get_tuning(int ydtype, int xkind, int binmode, int64_t n_in, mmlttb_tuning* tuning) {
+  if (!tuning) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  if (!tune_key_ok(d, ydtype, xkind, binmode & ~MMLTTB_NAN_AWARE)) return MMLTTB_EINVAL;
+  *tuning = tuning_for(d, ydtype, xkind, binmode, n_in);
+  return MMLTTB_OK;
+}
+
+int mmlttb_clear_tunings(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  memset(g_tune_set, 0, sizeof(g_tune_set));
+  return MMLTTB_OK;
+}
+
+int mmlttb_autotune_tuple(int ydtype, const void* y, int xkind, const void* x, int64_t n_in, int64_t n_out,
+                          int32_t r_ps, int binmode, int64_t* out_idx, int64_t out_cap, void* workspace,
+                          size_t workspace_bytes, mmlttb_stream stream, mmlttb_tuning* best, float* best_ms) {
+  if (!best) return MMLTTB_EINVAL;
+  DevInfo d;
+  int rc = get_dev_info(&d);
+  if (rc) return rc;
+  if (!tune_key_ok(d, ydtype, xkind, binmode & ~MMLTTB_NAN_AWARE)) return MMLTTB_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(e);
+  }
+  mmlttb_tuning cand{0, 0, 0, 0}, win{0, 0, 0, 0};
+  float win_ms = 3.0e38f;
+  const int saved_path = g_path_override;
+  g_path_override = MMLTTB_PATH_SPLIT;  // the stream and k_tables as kernels of their own
+  g_tune_override = &cand;
+  // the median of 7 timed runs after 3 untimed ones: the stream kernel (events armed
+  // around it) or, with whole = true, the whole call
+  auto timed = [&](int op, bool whole, float* ms) -> int {
+    float t[7];
+    for (int r = 0; r < 10; ++r) {
+      if (r >= 3 && !whole) {
+        g_ev_start = a;
+        g_ev_stop = b;
+      }
+      if (r >= 3 && whole && (e = cudaEventRecord(a, st)) != cudaSuccess) return cuda_fail(e);
+      int q = run_single(op, y, ydtype, x, xkind, n_in, n_out, r_ps, binmode, out_idx, out_cap, nullptr, workspace,
+                         workspace_bytes, st);
+      g_ev_start = g_ev_stop = nullptr;
+      if (q) return q;
+      if (r >= 3 && whole && (e = cudaEventRecord(b, st)) != cudaSuccess) return cuda_fail(e);
+      if (r >= 3) {
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaEventElapsedTime(&t[r - 3], a, b)) != cudaSuccess) return cuda_fail(e);
+      }
+    }
+    std::sort(t, t + 7);
+    *ms = t[3];
+    return MMLTTB_OK;
+  };
+  for (int v = 0; v < kStreamVariants && !rc; ++v)
+    for (int g = -1; g <= 1 && !rc; ++g) {
+      cand = mmlttb_tuning{v, g, 0, 0};
+      float ms = 0.0f;
+      rc = timed(MMLTTB_OP_PRESELECT, false, &ms);
+      if (!rc && ms < win_ms) {
+        win_ms = ms;
+        win = cand;
+      }
+    }
+  float best_whole = 3.0e38f;
+  const int rounds[4] = {0, 2, 4, 7};
+  mmlttb_tuning win2 = win;
+  for (int i = 0; i < 4 && !rc; ++i) {
+    cand = win;
+    cand.tab_rounds = rounds[i];
+    float ms = 0.0f;
+    rc = timed(MMLTTB_OP_MINMAXLTTB, true, &ms);
+    if (!rc && ms < best_whole) {
+      best_whole = ms;
+      win2 = cand;
+    }
+  }
+  g_tune_override = nullptr;
+  g_path_override = saved_path;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  rc = mmlttb_set_tuning(ydtype, xkind, binmode, n_in, &win2);
+  if (rc) return rc;
+  *best = win2;
+  if (best_ms) *best_ms = win_ms;
   return MMLTTB_OK;
 }
 

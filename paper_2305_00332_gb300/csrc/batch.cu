@@ -33,6 +33,30 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
     if (b->descs[s].n_in > 0) y_bytes += b->descs[s].n_in * (b->descs[s].ydtype == MMLTTB_F32 ? 4 : 8);
   const bool throughput = y_bytes >= kStreamThroughputBytes;
   const bool bulk_on = bulk_enabled();
+  // the tuning of the key (y type, x kind, bin mode) that holds most binned points, its
+  // size class from the batch's binned points
+  int64_t key_pts[2][3][2] = {};
+  int64_t binned_pts = 0;
+  for (int64_t s = 0; s < n; ++s) {
+    const mmlttb_series_desc& D = b->descs[s];
+    int32_t br;
+    int64_t B;
+    const int bm = D.binmode & ~MMLTTB_NAN_AWARE;
+    if (classify(D.op, D.ydtype, D.xkind, D.n_in, D.n_out, D.r_ps, D.binmode, &br, &B) || !binned(br)) continue;
+    key_pts[D.ydtype][D.xkind][bm] += D.n_in;
+    binned_pts += D.n_in;
+  }
+  int ky = MMLTTB_F32, kx = MMLTTB_X_IMPLICIT, kb = MMLTTB_BINS_INDEX;
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < 3; ++c)
+      for (int e = 0; e < 2; ++e)
+        if (key_pts[a][c][e] > key_pts[ky][kx][kb]) {
+          ky = a;
+          kx = c;
+          kb = e;
+        }
+  const mmlttb_tuning tu = tuning_for(d, ky, kx, kb, binned_pts);
+  b->tuning = tu;
   for (int64_t s = 0; s < n; ++s) {
     const mmlttb_series_desc& D = b->descs[s];
     int32_t br;
@@ -70,7 +94,7 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
     sp.nb = br == BR_M4 ? D.n_in : (D.n_in > 2 ? D.n_in - 2 : 0);
     // x-width bins can be very uneven: keep whole warps per bin there
     const int eb = D.ydtype == MMLTTB_F32 ? 4 : 8;
-    sp.group = sp.binmode == MMLTTB_BINS_XWIDTH ? 32 : stream_group(sp.nb, B, eb, throughput);
+    sp.group = sp.binmode == MMLTTB_BINS_XWIDTH ? 32 : shift_group(stream_group(sp.nb, B, eb, throughput), tu.group_shift);
     sp.tcost_off = tcost;
     if (mm && throughput && bulk_on && sp.binmode == MMLTTB_BINS_INDEX && D.ydtype == MMLTTB_F32)
       sp.bulk_bpt = bulk_bins_per_tile(sp.nb, B, eb);
@@ -120,11 +144,7 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
   b->total_edges = edges;
   b->total_slots = slots;
   b->total_bin_ctas = ctas;
-  // the variant tuned for the y type that holds most of the batch's points
-  int64_t pts[2] = {0, 0};
-  for (int64_t s = 0; s < n; ++s)
-    if (binned(b->plans[s].branch)) pts[b->plans[s].ydt == MMLTTB_F32 ? 0 : 1] += b->plans[s].nb;
-  b->variant = stream_variant(d, pts[1] > pts[0] ? MMLTTB_F64 : MMLTTB_F32);
+  b->variant = tu.variant;
   b->ymode = -1;  // the specialised stream kernel when every binned series shares one y mode
   for (int64_t s = 0; s < n; ++s) {
     const SeriesPlan& sp = b->plans[s];
@@ -217,6 +237,7 @@ static Batch batch_args(const BatchImpl* b, void* ws) {
   bt.tab_offs = (const int64_t*)(w + b->off_tab);
   bt.cta_offs = (const int64_t*)(w + b->off_cta);
   bt.tcost_offs = (const int64_t*)(w + b->off_tcost);
+  bt.tab_rounds_req = b->tuning.tab_rounds;
   bt.total_tcost = b->total_tcost;
   bt.n_bulk_warps = b->Wb;
   bt.total_bin_ctas = b->total_bin_ctas;
@@ -260,8 +281,7 @@ int batch_enqueue(BatchImpl* b, void* ws, cudaStream_t st) {
   }
   stage_mark(st);
   if (b->W > 0) {
-    const int64_t grid = (b->W + kStreamWarps - 1) / kStreamWarps;
-    if ((e = launch_stream(bt, grid, b->variant, b->ymode, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_stream(bt, b->variant, b->ymode, st)) != cudaSuccess) return cuda_fail(e);
     ++g_launches;
   }
   // the staged stream after the register stream: launched first, its resident CTAs
@@ -318,6 +338,12 @@ int mmlttb_batch_create(const mmlttb_series_desc* descs, int64_t n_series, mmltt
     return rc;
   }
   *out = b;
+  return MMLTTB_OK;
+}
+
+int mmlttb_batch_tuning(mmlttb_batch_t batch, mmlttb_tuning* tuning) {
+  if (!batch || !tuning) return MMLTTB_EINVAL;
+  *tuning = batch->impl.tuning;
   return MMLTTB_OK;
 }
 

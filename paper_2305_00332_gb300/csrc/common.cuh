@@ -44,8 +44,6 @@ __host__ __device__ inline int64_t staged_tab_bytes(int64_t m) {
 // Bins per CTA of the compaction kernels; every series' bins start on a CTA boundary.
 constexpr int kBinsPerCta = 256;
 // Threads of the streaming MinMax kernel's CTAs.
-constexpr int kStreamThreads = 256;
-constexpr int kStreamWarps = kStreamThreads / 32;
 // Staged stream (k_stream_bulk) for float32 index bins of at most kBulkMaxBinBytes:
 // every warp runs its own pipeline of kBulkStages shared-memory stages, each filled by
 // one cp.async.bulk copy of a tile (whole bins of one series, at most kBulkTileBytes
@@ -177,7 +175,8 @@ struct Batch {
   int64_t* fused_tot;  // per CTA of the fused kernel: indices its bins emit
   int64_t chain_smem;  // dynamic shared memory of k_chain for the tables (bytes)
   int32_t zero_status; // the launch clears the status and barrier words first (first kernel of a call)
-  int32_t tab_rounds;  // k_tables: rounds of 32 slots per warp (1..kTableRounds)
+  int32_t tab_rounds;  // k_tables: rounds of 32 slots per warp (1..kTableRoundsMax)
+  int32_t tab_rounds_req;  // the tuning's rounds for k_tables (0: from the slot count)
   const int64_t* tcost_offs;  // n_series+1 prefix of the staged stream's tile costs (NULL: single)
   int64_t total_tcost;  // the tile cost space k_stream_bulk's warps split evenly
   int64_t n_bulk_warps; // warps of k_stream_bulk
@@ -489,11 +488,13 @@ inline cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, size_t smem, cuda
   return cudaLaunchKernelEx(&cfg, kernel, bt);
 }
 cudaError_t launch_edges(const Batch& bt, cudaStream_t st);
-// Stream-kernel variants (see stream_variant_info); launch_stream runs one of them.
-constexpr int kStreamVariants = 3;
+constexpr int kTableRoundsMax = 7;  // k_tables: rounds of 32 slots per warp at most
+// Stream-kernel variants (see stream_variant_info); launch_stream runs one of them
+// over bt.n_warps warps.
+constexpr int kStreamVariants = 6;
 // ymode: 0 any y (dispatch per series), 1 float32 only, 2 float64 only, 3 float32
 // NaN-aware only, 4 float64 NaN-aware only; see stream_ymode.
-cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode, cudaStream_t st);
+cudaError_t launch_stream(const Batch& bt, int variant, int ymode, cudaStream_t st);
 // The staged stream over the series with bulk_bpt > 0 (bt.n_bulk_warps warps), and
 // its resident CTAs per SM.
 cudaError_t launch_stream_bulk(const Batch& bt, int ymode, cudaStream_t st);
@@ -505,6 +506,7 @@ inline int stream_ymode(int ydt, bool nan_aware) {
   return ydt == MMLTTB_F32 ? 1 : 2;
 }
 int stream_variant_info(int variant, int* unroll, int* min_blocks);
+int stream_variant_threads(int variant);  // threads per CTA
 // Compaction (A-2): per-bin resolve, per-series scan of CTA totals, placement.
 cudaError_t launch_compact(const Batch& bt, cudaStream_t st);
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st);

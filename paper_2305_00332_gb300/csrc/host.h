@@ -30,6 +30,12 @@ struct DevInfo {
 int get_dev_info(DevInfo* out);
 // Stream variant used for y of type ydt on this device (tuned or default).
 int stream_variant(const DevInfo& d, int ydt);
+// The tuning of a key (mmlttb_tuning; the thread's override while tuning, else the
+// stored one, else the default), the lanes-per-bin shift it applies, and the size
+// class of n (its decimal digits less one, at most 12).
+mmlttb_tuning tuning_for(const DevInfo& d, int ydt, int xk, int binmode, int64_t n);
+int shift_group(int G, int shift);
+int size_class(int64_t n);
 // Most streaming warps any variant runs (sizes the record array).
 int64_t stream_warp_cap(const DevInfo& d);
 // Streaming warps of `variant` for `work` units: every warp gets at least one point.
@@ -65,6 +71,7 @@ struct BatchImpl {
   int64_t Wcap = 0, W = 0;
   int64_t total_tcost = 0, Wb = 0;  // staged stream: tile cost space and warps
   int variant = 0;
+  mmlttb_tuning tuning = {0, 0, 0, 0};  // the tuning the batch was planned with
   int ymode = 0;  // stream-kernel y mode (stream_ymode) shared by every binned series, else 0
   bool any_block = false;
   int64_t max_tab = 0;  // largest per-series table storage (positions)

@@ -136,14 +136,15 @@ cudaError_t launch_barrier_probe(const Batch& bt, cudaStream_t st) {
 
 cudaError_t launch_tables(const Batch& bt, cudaStream_t st) {
   if (bt.total_slots <= 0) return cudaSuccess;
-  // as many rounds per warp as keep about 16 warps per SM busy, at most kTableRounds
+  // the tuning's rounds, else as many rounds per warp as keep about 16 warps per SM
+  // busy, at most kTableRounds
   int dev = 0, sms = 152;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   Batch b = bt;
-  const int64_t r = bt.total_slots / ((int64_t)sms * 16 * 32);
+  const int64_t r = bt.tab_rounds_req > 0 ? bt.tab_rounds_req : bt.total_slots / ((int64_t)sms * 16 * 32);
   b.tab_rounds = (int32_t)(r < 1 ? 1 : r > kTableRounds ? kTableRounds : r);
   const int64_t per_cta = (int64_t)(kTableThreads / 32) * 32 * b.tab_rounds;
   const int64_t grid = (bt.total_slots + per_cta - 1) / per_cta;

@@ -179,7 +179,7 @@ __device__ __forceinline__ void next_bucket(int64_t j, const Div& dK, int64_t N,
 
 // Slots a warp of k_tables fills: up to kTableRounds rounds of 32 (bt.tab_rounds; one
 // round when there are too few slots to fill the GPU).
-constexpr int kTableRounds = 7;
+constexpr int kTableRounds = kTableRoundsMax;
 constexpr int kTableBlock = 32 * kTableRounds;
 constexpr int kTableCache = 8;  // candidates kept in shared memory per bucket
 

@@ -10,12 +10,12 @@ namespace mmlttb {
 
 namespace {
 
-template <int U, int MINB, int kY>
-__global__ void __launch_bounds__(kStreamThreads, MINB) k_stream(const __grid_constant__ Batch bt) {
+template <int U, int MINB, int kY, int NT>
+__global__ void __launch_bounds__(NT, MINB) k_stream(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
   if (bt.zero_status && blockIdx.x == 0 && threadIdx.x == 0) zero_header(bt);
-  const int64_t w = (int64_t)blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   if (w >= bt.n_warps) return;
   stream_warp<U, kY>(bt, w, threadIdx.x & 31);
 }
@@ -50,14 +50,21 @@ __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt)
 
 }  // namespace
 
-// The compiled variants: (U, MINB) = (4, 4), (8, 3), (2, 6), each for any y and for
-// float32 and float64 y with and without the NaN-aware rule.
+// The compiled variants (loads in flight per lane U, CTAs per SM MINB, threads per CTA
+// NT): (4, 4, 256), (8, 3, 256), (2, 6, 256), (4, 8, 128), (8, 6, 128), (2, 12, 128),
+// each for any y and for float32 and float64 y with and without the NaN-aware rule.
+constexpr int kVarU[kStreamVariants] = {4, 8, 2, 4, 8, 2};
+constexpr int kVarMinB[kStreamVariants] = {4, 3, 6, 8, 6, 12};
+constexpr int kVarThreads[kStreamVariants] = {256, 256, 256, 128, 128, 128};
 template <int kY>
 static const void* stream_kernel_y(int v) {
   switch (v) {
-    case 1: return (const void*)k_stream<8, 3, kY>;
-    case 2: return (const void*)k_stream<2, 6, kY>;
-    default: return (const void*)k_stream<4, 4, kY>;
+    case 1: return (const void*)k_stream<8, 3, kY, 256>;
+    case 2: return (const void*)k_stream<2, 6, kY, 256>;
+    case 3: return (const void*)k_stream<4, 8, kY, 128>;
+    case 4: return (const void*)k_stream<8, 6, kY, 128>;
+    case 5: return (const void*)k_stream<2, 12, kY, 128>;
+    default: return (const void*)k_stream<4, 4, kY, 256>;
   }
 }
 static const void* stream_kernel(int v, int ymode) {
@@ -71,19 +78,19 @@ static const void* stream_kernel(int v, int ymode) {
 }
 
 int stream_variant_info(int v, int* unroll, int* min_blocks) {
-  static const int U[kStreamVariants] = {4, 8, 2}, M[kStreamVariants] = {4, 3, 6};
   if (v < 0 || v >= kStreamVariants) return -1;
-  *unroll = U[v];
-  *min_blocks = M[v];
+  *unroll = kVarU[v];
+  *min_blocks = kVarMinB[v];
   return 0;
 }
+
+int stream_variant_threads(int v) { return v >= 0 && v < kStreamVariants ? kVarThreads[v] : 256; }
 
 int stream_blocks_per_sm(int v) {
   int bps = 0;
   int b0 = 0;
   for (int y = kYAny; y <= kYF64Nan; ++y) {  // the smallest occupancy of the variant's kernels
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v, y), kStreamThreads, 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, stream_kernel(v, y), kVarThreads[v], 0) != cudaSuccess)
       return 1;
     if (y == kYAny || bps < b0) b0 = bps;
   }
@@ -98,23 +105,29 @@ cudaError_t launch_edges(const Batch& bt, cudaStream_t st) {
 }
 
 template <int kY>
-static cudaError_t launch_stream_y(const Batch& bt, dim3 g, dim3 b, int variant, cudaStream_t st) {
+static cudaError_t launch_stream_y(const Batch& bt, int64_t grid, int variant, cudaStream_t st) {
+  const dim3 g((unsigned)grid), b(kVarThreads[variant]);
   switch (variant) {
-    case 1: return launch_pdl(k_stream<8, 3, kY>, g, b, 0, st, bt);
-    case 2: return launch_pdl(k_stream<2, 6, kY>, g, b, 0, st, bt);
-    default: return launch_pdl(k_stream<4, 4, kY>, g, b, 0, st, bt);
+    case 1: return launch_pdl(k_stream<8, 3, kY, 256>, g, b, 0, st, bt);
+    case 2: return launch_pdl(k_stream<2, 6, kY, 256>, g, b, 0, st, bt);
+    case 3: return launch_pdl(k_stream<4, 8, kY, 128>, g, b, 0, st, bt);
+    case 4: return launch_pdl(k_stream<8, 6, kY, 128>, g, b, 0, st, bt);
+    case 5: return launch_pdl(k_stream<2, 12, kY, 128>, g, b, 0, st, bt);
+    default: return launch_pdl(k_stream<4, 4, kY, 256>, g, b, 0, st, bt);
   }
 }
 
-cudaError_t launch_stream(const Batch& bt, int64_t grid, int variant, int ymode, cudaStream_t st) {
+cudaError_t launch_stream(const Batch& bt, int variant, int ymode, cudaStream_t st) {
   if (bt.n_warps <= 0) return cudaSuccess;
-  const dim3 g((unsigned)grid), b(kStreamThreads);
+  if (variant < 0 || variant >= kStreamVariants) variant = 0;
+  const int wpc = kVarThreads[variant] / 32;
+  const int64_t grid = (bt.n_warps + wpc - 1) / wpc;
   switch (ymode) {
-    case kYF32: return launch_stream_y<kYF32>(bt, g, b, variant, st);
-    case kYF64: return launch_stream_y<kYF64>(bt, g, b, variant, st);
-    case kYF32Nan: return launch_stream_y<kYF32Nan>(bt, g, b, variant, st);
-    case kYF64Nan: return launch_stream_y<kYF64Nan>(bt, g, b, variant, st);
-    default: return launch_stream_y<kYAny>(bt, g, b, variant, st);
+    case kYF32: return launch_stream_y<kYF32>(bt, grid, variant, st);
+    case kYF64: return launch_stream_y<kYF64>(bt, grid, variant, st);
+    case kYF32Nan: return launch_stream_y<kYF32Nan>(bt, grid, variant, st);
+    case kYF64Nan: return launch_stream_y<kYF64Nan>(bt, grid, variant, st);
+    default: return launch_stream_y<kYAny>(bt, grid, variant, st);
   }
 }
 

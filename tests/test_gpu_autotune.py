@@ -49,3 +49,75 @@ def test_autotune_picks_a_variant(mm, tmp_path, monkeypatch):
     assert mm.lib.mmlttb_get_stream_variant(mm.F32, ctypes.byref(got)) == mm.OK and got.value == v
     assert mm.load_tuning() == {"f32": v}
     assert mm.lib.mmlttb_set_stream_variant(mm.F32, 0) == mm.OK
+
+
+def _mixed_tuning_batch():
+    """Float32 index-bin series (the batch's key) of many sizes, plus float64 x-width
+    and plain-LTTB series."""
+    r = np.random.default_rng(40)
+    series = []
+    for i in range(24):
+        n = int(10 ** r.uniform(3, 6.3))
+        series.append({"y_h": synth.random_walk(n, seed=400 + i, dtype=np.float32),
+                       "n_out": int(r.integers(50, 3000)), "r_ps": int(r.choice([2, 4, 8]))})
+    x = synth.exp_gaps_x(300_001, seed=41, mean_gap=20.0, big_gaps=2, big_gap=10**5)
+    series.append({"y_h": synth.random_walk(300_001, seed=42, dtype=np.float64), "x_h": x,
+                   "n_out": 900, "r_ps": 4, "binmode": "xwidth"})
+    series.append({"y_h": synth.random_walk(5000, seed=43, dtype=np.float32), "n_out": 700, "r_ps": 4,
+                   "op": "lttb"})
+    return series
+
+
+def test_every_tuple_matches_oracle_on_a_mixed_batch(mm, ref):
+    """Every tuning tuple (variant x lanes-per-bin shift x k_tables rounds) set for the
+    batch's key plans the batch with that tuple and returns the oracle's indices."""
+    series = _mixed_tuning_batch()
+    spec, exp = [], []
+    for s in series:
+        d = {"y": torch.from_numpy(s["y_h"]).cuda(), "n_out": s["n_out"], "r_ps": s["r_ps"],
+             "op": s.get("op", "minmaxlttb")}
+        if "x_h" in s:
+            d["x"] = torch.from_numpy(s["x_h"]).cuda()
+            d["binmode"] = s["binmode"]
+        spec.append(d)
+        if d["op"] == "lttb":
+            exp.append(ref.lttb(s["y_h"], s["n_out"]))
+        else:
+            exp.append(ref.minmaxlttb(s["y_h"], s["n_out"], s["r_ps"], x=s.get("x_h"),
+                                      binmode=s.get("binmode", "index")))
+    binned = sum(len(s["y_h"]) for s in series if s.get("op", "minmaxlttb") != "lttb")
+    try:
+        for v in range(len(mm.stream_variants())):
+            for g in (-1, 0, 1):
+                for rounds in (0, 1, 3, 7):
+                    mm.clear_tunings()
+                    mm.set_tuning(mm.F32, mm.X_IMPLICIT, mm.BINS_INDEX, binned, v, g, rounds)
+                    b = mm.Batch(spec)
+                    assert b.tuning() == {"variant": v, "group_shift": g, "tab_rounds": rounds}
+                    b.run(graph=(rounds == 3))
+                    for i, r in enumerate(b.results()):
+                        assert np.array_equal(r.cpu().numpy(), exp[i]), (v, g, rounds, i)
+                    b.close()
+    finally:
+        mm.clear_tunings()
+
+
+def test_autotune_tuple_keys_and_cache(mm, ref, tmp_path, monkeypatch):
+    monkeypatch.setenv("MMLTTB_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n = 20_000_003
+    y_h = synth.random_walk(n, seed=44, dtype=np.float32)
+    y = torch.from_numpy(y_h).cuda()
+    try:
+        t, ms = mm.autotune_tuple(y, n_out=4000, r_ps=4)
+        assert 0 <= t["variant"] < len(mm.stream_variants()) and t["group_shift"] in (-1, 0, 1)
+        assert t["tab_rounds"] in (0, 2, 4, 7) and ms > 0.0
+        assert mm.get_tuning(mm.F32, mm.X_IMPLICIT, mm.BINS_INDEX, n) == t
+        # another size class or key keeps the default
+        assert mm.get_tuning(mm.F32, mm.X_IMPLICIT, mm.BINS_INDEX, n // 100)["group_shift"] == 0
+        assert np.array_equal(mm.minmaxlttb(y, 4000, 4).cpu().numpy(), ref.minmaxlttb(y_h, 4000, 4))
+        mm.clear_tunings()
+        applied = mm.load_tuning()
+        assert t in applied.values()
+        assert mm.get_tuning(mm.F32, mm.X_IMPLICIT, mm.BINS_INDEX, n) == t
+    finally:
+        mm.clear_tunings()
