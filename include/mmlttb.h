@@ -379,7 +379,8 @@ int mmlttb_set_stage_events(void *const *events, int count);
  * kind, the bin mode and the size class (the decimal digits of n_in less one, at most
  * 12).  Single-series calls use the tuning of their key; a batch, the one of the key
  * that holds most of its binned points, its size class from its total points
- * (mmlttb_batch_tuning reports it).  Keys never set use the default {0 or the variant
+ * (mmlttb_batch_tuning reports it, mmlttb_batch_tuning_key that key with the batch's
+ * binned points as n_in).  Keys never set use the default {0 or the variant
  * set for the y type by mmlttb_set_stream_variant, 0, 0}.
  * mmlttb_autotune_tuple times, blocking, every variant x group_shift on MinMax
  * preselection of the caller's series (device y and, for int64/float64 x, x; n_in,
@@ -410,6 +411,7 @@ int mmlttb_set_tuning(int ydtype, int xkind, int binmode, int64_t n_in, const mm
 int mmlttb_get_tuning(int ydtype, int xkind, int binmode, int64_t n_in, mmlttb_tuning *tuning);
 int mmlttb_clear_tunings(void);
 int mmlttb_batch_tuning(mmlttb_batch_t batch, mmlttb_tuning *tuning);
+int mmlttb_batch_tuning_key(mmlttb_batch_t batch, int *ydtype, int *xkind, int *binmode, int64_t *n_in);
 int mmlttb_get_stream_variant(int ydtype, int *variant);
 int mmlttb_set_stream_variant(int ydtype, int variant);
 

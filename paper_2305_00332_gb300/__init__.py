@@ -358,6 +358,8 @@ lib.mmlttb_get_tuning.argtypes = [_int, _int, _int, _i64, ctypes.POINTER(Tuning)
 lib.mmlttb_autotune_tuple.argtypes = [_int, _vp, _int, _vp, _i64, _i64, _i32, _int, _vp, _i64, _vp, _sz, _vp,
                                       ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]
 lib.mmlttb_batch_tuning.argtypes = [_vp, ctypes.POINTER(Tuning)]
+lib.mmlttb_batch_tuning_key.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                        ctypes.POINTER(_i64)]
 
 
 def stream_variant_threads(variant):
@@ -424,6 +426,40 @@ def autotune_tuple(y, n_out=4000, r_ps=4, x=None, binmode=BINS_INDEX, save=True)
         with open(path, "w") as f:
             json.dump(cache, f, indent=1)
     return t.as_dict(), ms.value
+
+
+def autotune_batch(series, steps=10, warmup=3, shifts=(-1, 0, 1), rounds=(0, 2, 4, 7)):
+    """Time the CUDA-graph replay of a batch of `series` (as for Batch) planned with
+    every tuning tuple (stream variants x lanes-per-bin shifts x k_tables rounds), keep
+    the fastest for the batch's tuning key, and return (tuning dict, median ms, all
+    timings)."""
+    b = Batch(series)
+    key = b.tuning_key()
+    b.close()
+    timings = {}
+    best, best_ms = None, float("inf")
+    for v in range(len(stream_variants())):
+        for g in shifts:
+            for r in rounds:
+                set_tuning(*key, v, g, r)
+                b = Batch(series)
+                for _ in range(warmup):
+                    b.run(graph=True)
+                ts = []
+                for _ in range(steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    b.run(graph=True)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                b.close()
+                ms = sorted(ts)[len(ts) // 2]
+                timings[(v, g, r)] = ms
+                if ms < best_ms:
+                    best, best_ms = (v, g, r), ms
+    set_tuning(*key, *best)
+    return {"variant": best[0], "group_shift": best[1], "tab_rounds": best[2]}, best_ms, timings
 
 
 def load_tuning(device=None):
@@ -693,6 +729,13 @@ class Batch:
         t = Tuning()
         _check(lib.mmlttb_batch_tuning(self._h, ctypes.byref(t)), "mmlttb_batch_tuning")
         return t.as_dict()
+
+    def tuning_key(self):
+        """(y type, x kind, bin mode, n_in) of the tuning key the batch was planned under."""
+        a, b, c, n = _int(0), _int(0), _int(0), _i64(0)
+        _check(lib.mmlttb_batch_tuning_key(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                           ctypes.byref(n)), "mmlttb_batch_tuning_key")
+        return a.value, b.value, c.value, n.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -57,6 +57,10 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
         }
   const mmlttb_tuning tu = tuning_for(d, ky, kx, kb, binned_pts);
   b->tuning = tu;
+  b->key_ydt = ky;
+  b->key_xk = kx;
+  b->key_bm = kb;
+  b->key_n = binned_pts;
   for (int64_t s = 0; s < n; ++s) {
     const mmlttb_series_desc& D = b->descs[s];
     int32_t br;
@@ -344,6 +348,15 @@ int mmlttb_batch_create(const mmlttb_series_desc* descs, int64_t n_series, mmltt
 int mmlttb_batch_tuning(mmlttb_batch_t batch, mmlttb_tuning* tuning) {
   if (!batch || !tuning) return MMLTTB_EINVAL;
   *tuning = batch->impl.tuning;
+  return MMLTTB_OK;
+}
+
+int mmlttb_batch_tuning_key(mmlttb_batch_t batch, int* ydtype, int* xkind, int* binmode, int64_t* n_in) {
+  if (!batch || !ydtype || !xkind || !binmode || !n_in) return MMLTTB_EINVAL;
+  *ydtype = batch->impl.key_ydt;
+  *xkind = batch->impl.key_xk;
+  *binmode = batch->impl.key_bm;
+  *n_in = batch->impl.key_n;
   return MMLTTB_OK;
 }
 

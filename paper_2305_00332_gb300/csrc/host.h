@@ -72,6 +72,8 @@ struct BatchImpl {
   int64_t total_tcost = 0, Wb = 0;  // staged stream: tile cost space and warps
   int variant = 0;
   mmlttb_tuning tuning = {0, 0, 0, 0};  // the tuning the batch was planned with
+  int key_ydt = 0, key_xk = 0, key_bm = 0;  // its key: the (y type, x kind, bin mode) of most
+  int64_t key_n = 0;                        // binned points, and those points
   int ymode = 0;  // stream-kernel y mode (stream_ymode) shared by every binned series, else 0
   bool any_block = false;
   int64_t max_tab = 0;  // largest per-series table storage (positions)

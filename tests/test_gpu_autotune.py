@@ -121,3 +121,20 @@ def test_autotune_tuple_keys_and_cache(mm, ref, tmp_path, monkeypatch):
         assert mm.get_tuning(mm.F32, mm.X_IMPLICIT, mm.BINS_INDEX, n) == t
     finally:
         mm.clear_tunings()
+
+
+def test_autotune_batch_keeps_the_fastest_tuple(mm, ref):
+    series = _mixed_tuning_batch()[:12]
+    spec = [{"y": torch.from_numpy(s["y_h"]).cuda(), "n_out": s["n_out"], "r_ps": s["r_ps"]} for s in series]
+    try:
+        best, ms, timings = mm.autotune_batch(spec, steps=3, warmup=1, shifts=(0, 1), rounds=(0, 4))
+        assert len(timings) == len(mm.stream_variants()) * 4 and ms == min(timings.values())
+        b = mm.Batch(spec)
+        assert b.tuning() == best
+        b.run(graph=True)
+        for i, r in enumerate(b.results()):
+            assert np.array_equal(r.cpu().numpy(), ref.minmaxlttb(series[i]["y_h"], series[i]["n_out"],
+                                                                   series[i]["r_ps"])), i
+        b.close()
+    finally:
+        mm.clear_tunings()
