@@ -16,11 +16,14 @@ extern "C" {
 #endif
 
 #define MMLTTB_DIAG_FUSED_BARRIER 0 /* the fused kernel's grid barrier */
-#define MMLTTB_DIAG_GRID_BARRIER 1  /* the grid-wide LTTB engine's barrier */
+#define MMLTTB_DIAG_GRID_BARRIER 1  /* the large-bucket LTTB engine's grid barrier */
+#define MMLTTB_DIAG_MBARRIER 2      /* the staged MinMax stream's stage wait (mbarrier) */
 
 /*
- * Run one barrier of kind `which` on a two-CTA launch in which the second CTA never
- * arrives, so the first CTA's wait runs out after its 2 s bound.  `workspace` is a
+ * Run one wait of kind `which` that nothing satisfies: a grid barrier on a two-CTA
+ * launch in which the second CTA never arrives, or an mbarrier that expects one
+ * arrival that never comes (no copy is issued), so the wait runs out after its 2 s
+ * bound.  `workspace` is a
  * device buffer of at least 256 bytes whose first 256 bytes (the header) are cleared
  * first; afterwards mmlttb_workspace_status reports bit 1 (a wait timed out).
  * Asynchronous on `stream` (the kernel runs about 2 s).  MMLTTB_EINVAL for an unknown

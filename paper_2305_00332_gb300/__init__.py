@@ -565,7 +565,7 @@ def visual_metrics(ref, img, margin=20):
 
 
 # ---- failure-detection diagnostics (include/mmlttb_diag.h) ----
-DIAG_FUSED_BARRIER, DIAG_GRID_BARRIER = 0, 1
+DIAG_FUSED_BARRIER, DIAG_GRID_BARRIER, DIAG_MBARRIER = 0, 1, 2
 lib.mmlttb_diag_wait_timeout.argtypes = [_int, _vp, _sz, _vp]
 
 

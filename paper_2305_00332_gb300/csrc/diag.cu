@@ -60,7 +60,8 @@ extern "C" int mmlttb_check_series(const void* y, int ydtype, const void* x, int
 
 extern "C" int mmlttb_diag_wait_timeout(int which, void* workspace, size_t workspace_bytes,
                                         mmlttb_stream stream) {
-  if (which != MMLTTB_DIAG_FUSED_BARRIER && which != MMLTTB_DIAG_GRID_BARRIER) return MMLTTB_EINVAL;
+  if (which != MMLTTB_DIAG_FUSED_BARRIER && which != MMLTTB_DIAG_GRID_BARRIER && which != MMLTTB_DIAG_MBARRIER)
+    return MMLTTB_EINVAL;
   if (!workspace || workspace_bytes < kHeader) return MMLTTB_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(workspace, 0, kHeader, st);
@@ -68,7 +69,9 @@ extern "C" int mmlttb_diag_wait_timeout(int which, void* workspace, size_t works
   Batch bt = {};
   bt.status = (unsigned*)workspace;
   bt.barrier = (unsigned*)((char*)workspace + 4);
-  e = which == MMLTTB_DIAG_FUSED_BARRIER ? launch_sync_probe(bt, st) : launch_barrier_probe(bt, st);
+  e = which == MMLTTB_DIAG_FUSED_BARRIER ? launch_sync_probe(bt, st)
+      : which == MMLTTB_DIAG_GRID_BARRIER ? launch_barrier_probe(bt, st)
+                                          : launch_mbarrier_probe(bt, st);
   if (e != cudaSuccess) return cuda_fail(e);
   ++g_launches;
   return MMLTTB_OK;

@@ -52,6 +52,7 @@ bool bulk_enabled();
 // Failure-detection probes (a bounded wait that nothing satisfies; see mmlttb_diag.h).
 cudaError_t launch_sync_probe(const Batch& bt, cudaStream_t st);     // fused.cu grid_sync
 cudaError_t launch_barrier_probe(const Batch& bt, cudaStream_t st);  // lttb.cu grid_barrier
+cudaError_t launch_mbarrier_probe(const Batch& bt, cudaStream_t st); // minmax.cu staged-stream wait
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kHeader = 256;  // workspace header: status word @0, barrier counter @4, m @8

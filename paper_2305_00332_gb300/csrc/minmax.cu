@@ -38,6 +38,20 @@ __global__ void __launch_bounds__(kBulkWarps * 32) k_stream_bulk(const __grid_co
   bulk_warp<kY>(bt, w, threadIdx.x & 31, sbase, bbase);
 }
 
+// Failure-detection probe of the staged stream's stage wait: one warp waits on an
+// mbarrier that expects one arrival, which never comes (no copy is issued), so the
+// bounded wait runs out (2 s); lane 0 sets status bit 1 and the kernel returns.
+__global__ void k_mbarrier_probe(unsigned* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (!mbar_wait_bounded(b, 0) && threadIdx.x == 0) atomicOr(status, 1u);
+}
+
 __global__ void __launch_bounds__(256) k_edges(const __grid_constant__ Batch bt) {
   pdl_wait();
   pdl_trigger();
@@ -159,6 +173,11 @@ int stream_bulk_blocks_per_sm() {
     if (i == 0 || bps < b0) b0 = bps;
   }
   return b0 > 0 ? b0 : 1;
+}
+
+cudaError_t launch_mbarrier_probe(const Batch& bt, cudaStream_t st) {
+  k_mbarrier_probe<<<1, 32, 0, st>>>(bt.status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stream_bulk(const Batch& bt, int ymode, cudaStream_t st) {

@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a fault: every device-side wait of the
-library is bounded, and a device-side check reports violated preconditions.  A barrier that one CTA never reaches runs out after its 2 s
-limit, the kernel records bit 1 in the workspace status word and returns, and the
-context stays usable: the next call returns the oracle's indices."""
+library is bounded, and a device-side check reports violated preconditions.  A grid
+barrier that one CTA never reaches, or a staged-stream mbarrier that no copy completes,
+runs out after its 2 s limit, the kernel records bit 1 in the workspace status word and
+returns, and the context stays usable: the next call returns the oracle's indices."""
 import numpy as np
 import pytest
 import torch
@@ -11,10 +12,10 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("which", ["fused", "grid"])
+@pytest.mark.parametrize("which", ["fused", "grid", "mbarrier"])
 def test_unsatisfied_barrier_times_out_and_reports(mm, ref, which):
     ws = torch.empty(256, dtype=torch.uint8, device="cuda")
-    kind = {"fused": mm.DIAG_FUSED_BARRIER, "grid": mm.DIAG_GRID_BARRIER}[which]
+    kind = {"fused": mm.DIAG_FUSED_BARRIER, "grid": mm.DIAG_GRID_BARRIER, "mbarrier": mm.DIAG_MBARRIER}[which]
     mm.diag_wait_timeout(kind, ws)
     assert mm.workspace_status(ws) == 1  # bit 1: a bounded wait timed out
     y = synth.random_walk(100_000, seed=3, dtype=np.float32)
