@@ -318,25 +318,6 @@ __device__ int table_pick(const SeriesPlan& sp, const TableChunk& ch, int i, int
   return pk;
 }
 
-// Table slot `slot` (one slot per position of every series, series s holding slots
-// from tab_offs[s]): whether it has an entry, and the bucket jt whose pick follows a
-// pick at its position (R1).
-__device__ __forceinline__ bool slot_bucket(const Batch& bt, int64_t slot, int s, int64_t* jt) {
-  if (slot >= bt.total_slots) return false;
-  const SeriesPlan& sp = plan_of(bt, s);
-  if (sp.engine != EN_TABLES) return false;
-  const int64_t p = slot - sp.tab_off, m = lttb_m(sp);
-  if (p >= m || m <= sp.n_out) return false;
-  const int64_t K = sp.n_out - 2;
-  if (p == 0) {
-    *jt = 0;
-  } else {
-    if (p > m - 2) return false;
-    *jt = part_of(p, m - 2, K) + 1;
-  }
-  return *jt < K;
-}
-
 // Table entries of the warp's block of slots [base, base + 32*rounds).  Warp-
 // collective; `s0` is the series of slot `base`; sh is the warp's shared memory.
 __device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, int lane, TableShared& sh) {
@@ -346,14 +327,43 @@ __device__ void table_block(const Batch& bt, int64_t base, int rounds, int s0, i
   int s = s0, nreq = 0;
   int64_t carry_jt = -1;
   int carry_s = -1;
+  // the lane's current series, cached: its next series' first slot, table offset,
+  // position count m, bucket count K and a divisor for m - 2 (no load or division per
+  // slot while the series stays the same)
+  int cs = -1;
+  int64_t c_next = 0, c_off = 0, c_m = 0, c_K = 0;
+  bool c_tab = false;
+  Div c_dN;
 #pragma unroll
   for (int r = 0; r < kTableRounds; ++r) {
     if (r >= rounds) continue;
     const int64_t slot = base + 32 * r + lane;
-    if (bt.tab_offs)
-      while (s + 1 < bt.n_series && bt.tab_offs[s + 1] <= slot) ++s;
+    if (cs < 0 || slot >= c_next) {
+      if (bt.tab_offs)
+        while (s + 1 < bt.n_series && bt.tab_offs[s + 1] <= slot) ++s;
+      const SeriesPlan& sp = plan_of(bt, s);
+      cs = s;
+      c_next = bt.tab_offs && s + 1 < bt.n_series ? bt.tab_offs[s + 1] : INT64_MAX;
+      c_off = sp.tab_off;
+      c_tab = sp.engine == EN_TABLES;
+      c_m = c_tab ? lttb_m(sp) : 0;
+      c_K = sp.n_out - 2;
+      c_tab = c_tab && c_m > sp.n_out;
+      c_dN = make_div(c_m - 2 > 0 ? c_m - 2 : 1);
+    }
     int64_t jt = -1;
-    const bool work = slot_bucket(bt, slot, s, &jt);
+    bool work = false;
+    if (slot < bt.total_slots && c_tab) {  // the bucket its pick falls in (R1): jt
+      const int64_t p = slot - c_off;
+      if (p == 0) {
+        jt = 0;
+        work = true;
+      } else if (p <= c_m - 2) {
+        jt = part_of(p, c_dN, c_K) + 1;
+        work = true;
+      }
+      work = work && jt < c_K;
+    }
     const int ks = work ? s : -1;
     int64_t pjt = __shfl_up_sync(kFull, work ? jt : -1, 1);
     int ps = __shfl_up_sync(kFull, ks, 1);
