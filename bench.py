@@ -167,6 +167,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
+class _one_core:
+    """Pin the calling thread to one core (the last it may run on) while the oracle is
+    timed; the core, or None where affinity cannot be set."""
+
+    def __enter__(self):
+        try:
+            self.old = os.sched_getaffinity(0)
+            core = max(self.old)
+            os.sched_setaffinity(0, {core})
+            return core
+        except (AttributeError, OSError, ValueError):
+            self.old = None
+            return None
+
+    def __exit__(self, *a):
+        if self.old is not None:
+            os.sched_setaffinity(0, self.old)
+
+
 def run_reference(args, ws, rank):
     """The oracle (single-threaded C) as the reference arm, on a bounded sample of the
     workload per step: the first S points of the same series, same n_out and r_ps."""
@@ -187,12 +206,13 @@ def run_reference(args, ws, rank):
         yn, xn = y.numpy(), x.numpy()
     else:
         yn, xn = yn[:S], xn[:S]
-    for _ in range(args.warmup):
-        o.minmaxlttb(yn, N_OUT, R_PS, x=xn, binmode="xwidth")
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        o.minmaxlttb(yn, N_OUT, R_PS, x=xn, binmode="xwidth")
-    el = time.perf_counter() - t
+    with _one_core() as core:
+        for _ in range(args.warmup):
+            o.minmaxlttb(yn, N_OUT, R_PS, x=xn, binmode="xwidth")
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            o.minmaxlttb(yn, N_OUT, R_PS, x=xn, binmode="xwidth")
+        el = time.perf_counter() - t
     v = S * args.steps / el / 1e9
     sample = f"first {S} points of the workload series per step (n_out=4000, r_ps=4, x-width bins)"
     print(json.dumps({
@@ -201,7 +221,8 @@ def run_reference(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n_in": args.n, "n_out": N_OUT, "r_ps": R_PS,
                                         "bins": "xwidth", "reference_sample_points": S},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "pinned_core": core, "nproc": os.cpu_count()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -351,12 +372,15 @@ def main():
     parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle
+        from bench_workloads import host_cpu, one_core
         o = oracle()
-        t = time.perf_counter()
-        ref = o.minmaxlttb(y_h.numpy(), N_OUT, R_PS, x=x_h.numpy(), binmode="xwidth")
-        el = time.perf_counter() - t
+        with one_core() as core:
+            t = time.perf_counter()
+            ref = o.minmaxlttb(y_h.numpy(), N_OUT, R_PS, x=x_h.numpy(), binmode="xwidth")
+            el = time.perf_counter() - t
         cpu = {"value": n / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full workload once ({n} points), single-threaded C oracle"}
+               "sample": f"the full workload once ({n} points), single-threaded C oracle",
+               "pinned_core": core, **host_cpu()}
         parity = "bit-exact" if np.array_equal(ref, res) else "MISMATCH"
 
     # the metric's other parts, on this GPU after the headline (single-GPU runs only):

@@ -18,14 +18,57 @@
                 the charts of MinMax, MinMaxLTTB (r_ps 2, 4, 6, 8), LTTB and M4 at n_out
                 200..2000 with their PEM_20 and MSE against the chart of all points.
 """
+import contextlib
 import ctypes
 import json
+import os
+import platform
+import subprocess
 import time
 
 import numpy as np
 import torch
 
 import synth
+
+
+def host_cpu():
+    """The host's CPU model and core count, for the oracle timings."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cpu_model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+@contextlib.contextmanager
+def one_core():
+    """Pin the calling thread to one core (the last it may run on) for an oracle timing;
+    yields the core, or None where affinity cannot be set."""
+    try:
+        old = os.sched_getaffinity(0)
+        core = max(old)
+        os.sched_setaffinity(0, {core})
+    except (AttributeError, OSError, ValueError):
+        old, core = None, None
+    try:
+        yield core
+    finally:
+        if old is not None:
+            os.sched_setaffinity(0, old)
 
 
 def _events(n):
@@ -172,17 +215,18 @@ def record_vs_plain_lttb(mm, steps, warmup, clock_index="0", oracle=True):
         o = load_oracle()
         g4 = mm.minmaxlttb(y, n_out, 4).cpu().numpy()
         gp = mm.lttb(y, n_out).cpu().numpy()
-        t = time.perf_counter()
-        e4 = o.minmaxlttb(y_h, n_out, 4)
-        c4 = time.perf_counter() - t
-        t = time.perf_counter()
-        ep = o.lttb(y_h, n_out)
-        cp = time.perf_counter() - t
+        with one_core() as core:
+            t = time.perf_counter()
+            e4 = o.minmaxlttb(y_h, n_out, 4)
+            c4 = time.perf_counter() - t
+            t = time.perf_counter()
+            ep = o.lttb(y_h, n_out)
+            cp = time.perf_counter() - t
         ok = np.array_equal(g4, e4) and np.array_equal(gp, ep)
         rec["parity_vs_oracle"] = "bit-exact" if ok else "MISMATCH"
         rec["cpu_baseline"] = {"value": n / c4 / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
                                "sample": "the full 1e8-point series once, MinMaxLTTB r_ps=4, single-threaded C oracle",
-                               "plain_lttb_s": cp}
+                               "plain_lttb_s": cp, "pinned_core": core, **host_cpu()}
     del y, ws
     torch.cuda.empty_cache()
     return rec
@@ -283,16 +327,19 @@ def record_batched(mm, steps, warmup, clock_index="0", oracle=True, singles_reps
         from oracle import oracle as load_oracle
         o = load_oracle()
         pts, el, ok = 0, 0.0, True
+        exp = {}
+        with one_core() as core:
+            for i in sample:
+                t = time.perf_counter()
+                exp[i] = o.minmaxlttb(ys_h[i], int(nouts[i]), 4)
+                el += time.perf_counter() - t
+                pts += int(lens[i])
         for i in sample:
-            t = time.perf_counter()
-            e = o.minmaxlttb(ys_h[i], int(nouts[i]), 4)
-            el += time.perf_counter() - t
-            pts += int(lens[i])
-            ok &= bool(np.array_equal(res[i].cpu().numpy(), e))
+            ok &= bool(np.array_equal(res[i].cpu().numpy(), exp[i]))
         rec["parity_vs_oracle"] = ("bit-exact" if ok else "MISMATCH") + f" on {len(sample)} sampled series"
         rec["cpu_baseline"] = {"value": pts / el / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
                                "sample": f"{len(sample)} seeded series of the batch ({pts} points), "
-                                         "single-threaded C oracle"}
+                                         "single-threaded C oracle", "pinned_core": core, **host_cpu()}
     b.close()
     del ys, outs, wss, res
     torch.cuda.empty_cache()
@@ -491,9 +538,10 @@ def run_visual(args, mm):
     from oracle import oracle
     o = oracle()
     S = 1_000_000
-    t = time.perf_counter()
-    o.raster(y_host[:S], ext, W, H)
-    cpu_s = time.perf_counter() - t
+    with one_core() as core:
+        t = time.perf_counter()
+        o.raster(y_host[:S], ext, W, H)
+        cpu_s = time.perf_counter() - t
     _line("reference line-chart rasterisation throughput (1e7 points, 800x250, 4x4 samples)",
           (n - 1) / (rmed * 1e-3) / 1e9, "Gsegments/s", True,
           {"workload": "line charts 800x250: 1e7-point float32 walk + sines + spikes (throughput); "
@@ -501,7 +549,8 @@ def run_visual(args, mm):
           {"dtype": "f32", "reference_chart_ms": rmed, "reference_chart_ms_back_to_back": rmean,
            "inked_pixels": inked, "gpu_launches": launches, **chart_ms, "pem20_mse_template_2e5": table,
            "cpu_baseline": {"value": (S - 1) / cpu_s / 1e9, "unit": "Gsegments/s", "cores": 1,
-                            "kind": "oracle", "sample": f"chart of the first {S} points, single-threaded C oracle"}},
+                            "kind": "oracle", "sample": f"chart of the first {S} points, single-threaded C oracle",
+                            "pinned_core": core, **host_cpu()}},
           args)
 
 
