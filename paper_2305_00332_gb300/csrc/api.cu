@@ -236,9 +236,11 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     const mmlttb_tuning tu = tuning_for(d, ydt, xk, binmode, n);
     p.variant = tu.variant;
     p.tab_rounds = tu.tab_rounds;
+    const bool large = N * eb >= kStreamThroughputBytes;
     p.group = binmode == MMLTTB_BINS_XWIDTH
                   ? 32
-                  : shift_group(stream_group(N, p.B, eb, N * eb >= kStreamThroughputBytes), tu.group_shift);
+                  : shift_group(large ? stream_group_single(N, p.B, eb) : stream_group(N, p.B, eb, false),
+                                tu.group_shift);
     if (binmode == MMLTTB_BINS_INDEX && ydt == MMLTTB_F32 && N * eb >= kStreamThroughputBytes && bulk_enabled())
       p.bulk_bpt = bulk_bins_per_tile(N, p.B, eb);
     if (p.bulk_bpt > 0) {  // the staged stream: no register-stream work

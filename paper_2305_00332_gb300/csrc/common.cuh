@@ -394,6 +394,23 @@ __host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes
   return G;
 }
 
+// Lanes per bin for a single series that streams at least kStreamThroughputBytes.
+// Alone on the GPU, small bins want more lanes than the batch rule gives: on 1e9
+// float32 points, 4 lanes for bins of 128 B to 1 KiB (125-point bins 2.5 -> 3.9 TB/s,
+// 256-point 2.9 -> 4.5) and 8 up to 4 KiB (512-point 4.2 -> 5.2), then about 512 bytes
+// per lane.  In a batch the same choice measured slower (its series share the work
+// space by a per-bin cost that grows with the lanes per bin), so batches keep
+// stream_group.
+__host__ __device__ inline int stream_group_single(int64_t N, int64_t B, int elem_bytes) {
+  const int64_t per_bin_bytes = (B > 0 ? N / B : N) * elem_bytes;
+  if (per_bin_bytes <= 128) return 1;
+  if (per_bin_bytes <= 1024) return 4;
+  if (per_bin_bytes <= 4096) return 8;
+  int G = 16;
+  while (G < 32 && (int64_t)G * 512 < per_bin_bytes) G <<= 1;
+  return G;
+}
+
 // Streaming warp w covers global work units [floor(w*T/W), floor((w+1)*T/W)).
 __host__ __device__ inline int64_t warp_begin(int64_t w, int64_t total, const Div& warps) {
   return muldiv(w, total, warps);
