@@ -170,7 +170,7 @@ int mmlttb_minmaxlttb(const void *y, int ydtype, const void *x, int xkind, int64
  *   Scratch: a 4 MiB array compiled into the library (a static __device__
  *   variable), so every GPU that loads the library holds those 4 MiB until the
  *   process exits.  Sizes whose workspace (mmlttb_workspace_bytes) exceeds 4 MiB
- *   return MMLTTB_ESCRATCH and enqueue nothing; about 38 000 MinMax bins
+ *   return MMLTTB_ESCRATCH and enqueue nothing; about 34 000 MinMax bins
  *   (n_out * r_ps / 2) fit.
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress, with that device current) and caches it; make that first

@@ -261,7 +261,7 @@ int plan_single(int op, int ydt, int xk, int64_t n, int64_t n_out, int32_t r_ps,
     off = align256(off + (size_t)(p.B + p.Wcap) * sizeof(Record));
     p.nct = (p.B + kBinsPerCta - 1) / kBinsPerCta;
     p.off_binres = off;
-    off = align256(off + (size_t)p.nct * kBinsPerCta * 16);
+    off = align256(off + (size_t)p.nct * kBinsPerCta * 32);
     p.off_ctasum = off;
     off = align256(off + (size_t)p.nct * 4);
     p.off_ctaser = off;

@@ -179,7 +179,7 @@ int batch_plan(BatchImpl* b, const DevInfo& d, char* lend, size_t lend_bytes) {
   b->off_sel = take((size_t)sel * 8);
   b->off_px = take((size_t)sel * 8);
   b->off_py = take((size_t)sel * 8);
-  b->off_binres = take((size_t)ctas * kBinsPerCta * 16);
+  b->off_binres = take((size_t)ctas * kBinsPerCta * 32);
   b->off_ctasum = take((size_t)ctas * 4);
   b->off_ctaser = take((size_t)ctas * 4);
   b->off_ctaoff = take((size_t)ctas * 8);

@@ -166,7 +166,7 @@ struct Batch {
   int64_t total_bin_ctas;  // compaction CTAs over all minmax series
   Record* rec;         // total bins + n_warps records
   int64_t* edges;      // bin starts S_b of x-width series
-  int64_t* binres;     // per padded bin: (first argmin/argmax lower, higher) or (-1, -1)
+  int64_t* binres;     // per padded bin: (first argmin/argmax lower, higher, their keys) or (-1, -1, 0, 0)
   int32_t* cta_sum;    // per compaction CTA: number of indices its bins emit
   int32_t* cta_series; // per compaction CTA: its series
   int64_t* cta_off;    // per compaction CTA: exclusive prefix of cta_sum within its series

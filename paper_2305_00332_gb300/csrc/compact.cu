@@ -3,12 +3,14 @@
 //
 // Every series' bins are laid out from a CTA boundary (kBinsPerCta bins per CTA).
 //   k_bins     one thread per bin: combine the bin's records (consecutive slots)
-//              into (lower, higher) of argmin/argmax, -1 for an empty bin; each CTA
+//              into (lower, higher) of argmin/argmax with their keys, -1 for an empty
+//              bin; each CTA
 //              writes how many indices its bins emit.
 //   k_binscan  one warp per series: exclusive scan of the series' CTA totals; the
 //              series' count m and the first and last entries of its list.
 //   k_place    one thread per bin: block scan + CTA offset place the bin's indices
-//              (and, before LTTB, their x and y as FP64) in the preselected list.
+//              (and, before LTTB, their x and y as FP64, y from the record keys) in
+//              the preselected list.
 #include "compact.cuh"
 
 namespace mmlttb {
@@ -26,10 +28,13 @@ __global__ void __launch_bounds__(kBinsPerCta) k_bins(const __grid_constant__ Ba
   const SeriesPlan& sp = plan_of(bt, s_series);
   const int64_t b = (c - sp.bincta_off) * kBinsPerCta + threadIdx.x;
   int64_t lo, hi, first, last;
-  resolve_bin(bt, sp, b, &lo, &hi, &first, &last);
+  long long klo, khi;
+  resolve_bin(bt, sp, b, &lo, &hi, &klo, &khi, &first, &last);
   const int64_t slot = c * kBinsPerCta + threadIdx.x;
-  bt.binres[2 * slot] = lo;
-  bt.binres[2 * slot + 1] = hi;
+  bt.binres[4 * slot] = lo;
+  bt.binres[4 * slot + 1] = hi;
+  bt.binres[4 * slot + 2] = klo;
+  bt.binres[4 * slot + 3] = khi;
   int cnt = bin_count(sp, lo, hi, first, last);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(kFull, cnt, d);
@@ -80,7 +85,8 @@ __global__ void __launch_bounds__(kBinsPerCta) k_place(const __grid_constant__ B
   const int s = bt.cta_series[c];
   const SeriesPlan& sp = plan_of(bt, s);
   const int64_t slot = c * kBinsPerCta + threadIdx.x;
-  const int64_t lo = bt.binres[2 * slot], hi = bt.binres[2 * slot + 1];
+  const int64_t lo = bt.binres[4 * slot], hi = bt.binres[4 * slot + 1];
+  const long long klo = bt.binres[4 * slot + 2], khi = bt.binres[4 * slot + 3];
   int64_t first = -1, last = -1;
   if (sp.branch == BR_M4 && lo >= 0) {
     const int64_t b = (c - sp.bincta_off) * kBinsPerCta + threadIdx.x;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(kBinsPerCta) k_place(const __grid_constant__ B
   const int cnt = bin_count(sp, lo, hi, first, last);
   int excl;
   block_excl_scan<kBinsPerCta>(cnt, &excl);
-  place_bin(sp, lo, hi, first, last, cnt, bt.cta_off[c] + excl);
+  place_bin(sp, lo, hi, klo, khi, first, last, cnt, bt.cta_off[c] + excl);
 }
 
 }  // namespace

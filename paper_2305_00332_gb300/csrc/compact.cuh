@@ -53,31 +53,50 @@ __device__ __forceinline__ int m4_count(int64_t first, int64_t lo, int64_t hi, i
   return lo < 0 ? 0 : 1 + (lo != first) + (hi != lo) + (last != hi);
 }
 
+// The y value (FP64) a record key stands for: keys are order-preserving images of the
+// values (key32 / key64), so this inverts them, with -0.0 coming back as +0.0 (they
+// compare equal, and every LTTB area takes an absolute value, so no pick changes).
+__device__ __forceinline__ double value_of_key(const SeriesPlan& sp, long long k) {
+  if (sp.ydt == MMLTTB_F32) {
+    const int k32 = (int)k;
+    const unsigned bits = k32 >= 0 ? (unsigned)k32 : ((0u - (unsigned)k32) | 0x80000000u);
+    return (double)__uint_as_float(bits);
+  }
+  const unsigned long long bits =
+      k >= 0 ? (unsigned long long)k : ((0ull - (unsigned long long)k) | 0x8000000000000000ull);
+  return __longlong_as_double((long long)bits);
+}
+
 // Resolve bin b of series sp from its records (consecutive slots, one per warp that
-// streamed part of it; one slot for a series of the staged stream): lo/hi = the lower and higher of (first argmin, first
-// argmax), first/last = the bin's first and last point; all -1 for an empty bin.
-__device__ __forceinline__ void resolve_bin(const Batch& bt, const SeriesPlan& sp, int64_t b,
-                                            int64_t* lo, int64_t* hi, int64_t* first, int64_t* last) {
+// streamed part of it; one slot for a series of the staged stream): lo/hi = the lower
+// and higher of (first argmin, first argmax) and klo/khi the record keys of their y
+// values, first/last = the bin's first and last point; all -1 (keys 0) for an empty bin.
+__device__ __forceinline__ void resolve_bin(const Batch& bt, const SeriesPlan& sp, int64_t b, int64_t* lo,
+                                            int64_t* hi, long long* klo, long long* khi, int64_t* first,
+                                            int64_t* last) {
   *lo = *hi = *first = *last = -1;
+  *klo = *khi = 0;
   if (sp.nb <= 0 || b >= sp.B) return;
   const int64_t sb = bin_start(bt, sp, b);
   const int64_t sb1 = (b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1);
   if (sb >= sb1) return;
   *first = sb;
   *last = sb1 - 1;
+  Record r;
   if (sp.bulk_bpt > 0) {  // staged stream: one record per bin
-    const Record r = bt.rec[sp.bin_off + b + sp.rec_w];
-    *lo = r.imin < r.imax ? r.imin : r.imax;
-    *hi = r.imin < r.imax ? r.imax : r.imin;
-    return;
+    r = bt.rec[sp.bin_off + b + sp.rec_w];
+  } else {
+    const int64_t wf = warp_of(sp.pos_off + muldiv(sb - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
+    const int64_t wl = warp_of(sp.pos_off + muldiv(sb1 - 1 - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
+    const Record* rb = bt.rec + sp.bin_off + b;
+    r = rb[wf];
+    for (int64_t w = wf + 1; w <= wl; ++w) combine(r, rb[w]);
   }
-  const int64_t wf = warp_of(sp.pos_off + muldiv(sb - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
-  const int64_t wl = warp_of(sp.pos_off + muldiv(sb1 - 1 - sp.p0, sp.npos, sp.dnb), bt.dtotal, bt.n_warps);
-  const Record* rb = bt.rec + sp.bin_off + b;
-  Record r = rb[wf];
-  for (int64_t w = wf + 1; w <= wl; ++w) combine(r, rb[w]);
-  *lo = r.imin < r.imax ? r.imin : r.imax;
-  *hi = r.imin < r.imax ? r.imax : r.imin;
+  const bool min_first = r.imin < r.imax;
+  *lo = min_first ? r.imin : r.imax;
+  *hi = min_first ? r.imax : r.imin;
+  *klo = min_first ? r.kmin : r.kmax;
+  *khi = min_first ? r.kmax : r.kmin;
 }
 
 // Indices bin b of series sp contributes to the list: MinMax (lo, hi) deduplicated
@@ -89,9 +108,9 @@ __device__ __forceinline__ int bin_count(const SeriesPlan& sp, int64_t lo, int64
 
 // Write bin b's indices at list offset o (the exclusive prefix of the counts of the
 // bins before it); MinMax lists start after the first point and carry FP64 copies of
-// x and y for LTTB.
-__device__ __forceinline__ void place_bin(const SeriesPlan& sp, int64_t lo, int64_t hi, int64_t first,
-                                          int64_t last, int cnt, int64_t o) {
+// x and y for LTTB, y from the record keys klo/khi (no gather of y).
+__device__ __forceinline__ void place_bin(const SeriesPlan& sp, int64_t lo, int64_t hi, long long klo,
+                                          long long khi, int64_t first, int64_t last, int cnt, int64_t o) {
   if (cnt == 0) return;
   if (sp.branch == BR_M4) {
     sp.sel[o++] = first;
@@ -106,10 +125,10 @@ __device__ __forceinline__ void place_bin(const SeriesPlan& sp, int64_t lo, int6
   if (cnt == 2) sp.sel[pos + 1] = hi;
   if (sp.px) {
     sp.px[pos] = x_of(sp, lo);
-    sp.py[pos] = y_of(sp, lo);
+    sp.py[pos] = value_of_key(sp, klo);
     if (cnt == 2) {
       sp.px[pos + 1] = x_of(sp, hi);
-      sp.py[pos + 1] = y_of(sp, hi);
+      sp.py[pos + 1] = value_of_key(sp, khi);
     }
   }
 }

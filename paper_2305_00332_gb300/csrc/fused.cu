@@ -247,9 +247,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
       const int64_t b = t + tid;
       if (b < b1) {
         int64_t lo, hi, first, last;
-        resolve_bin(bt, sp, b, &lo, &hi, &first, &last);
-        bt.binres[2 * b] = lo;
-        bt.binres[2 * b + 1] = hi;
+        long long klo, khi;
+        resolve_bin(bt, sp, b, &lo, &hi, &klo, &khi, &first, &last);
+        bt.binres[4 * b] = lo;
+        bt.binres[4 * b + 1] = hi;
+        bt.binres[4 * b + 2] = klo;
+        bt.binres[4 * b + 3] = khi;
         acc += bin_count(sp, lo, hi, first, last);
       }
     }
@@ -282,9 +285,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
     for (int64_t t = b0; t < b1; t += kFusedThreads) {
       const int64_t b = t + tid;
       int64_t lo = -1, hi = -1, first = -1, last = -1;
+      long long klo = 0, khi = 0;
       if (b < b1) {
-        lo = bt.binres[2 * b];
-        hi = bt.binres[2 * b + 1];
+        lo = bt.binres[4 * b];
+        hi = bt.binres[4 * b + 1];
+        klo = bt.binres[4 * b + 2];
+        khi = bt.binres[4 * b + 3];
         if (sp.branch == BR_M4 && lo >= 0) {
           first = bin_start(bt, sp, b);
           last = ((b + 1 >= sp.B) ? sp.p0 + sp.nb : bin_start(bt, sp, b + 1)) - 1;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(const __grid_constan
       const int cnt = bin_count(sp, lo, hi, first, last);
       int excl;
       const int tile = block_excl_scan<kFusedThreads>(cnt, &excl);
-      place_bin(sp, lo, hi, first, last, cnt, carry + excl);
+      place_bin(sp, lo, hi, klo, khi, first, last, cnt, carry + excl);
       carry += tile;
     }
     if (sp.branch == BR_PRESELECT || sp.branch == BR_M4 || sp.engine != EN_TABLES) return;
