@@ -398,9 +398,9 @@ __host__ __device__ inline int stream_group(int64_t N, int64_t B, int elem_bytes
 // Alone on the GPU, small bins want more lanes than the batch rule gives: on 1e9
 // float32 points, 4 lanes for bins of 128 B to 1 KiB (125-point bins 2.5 -> 3.9 TB/s,
 // 256-point 2.9 -> 4.5) and 8 up to 4 KiB (512-point 4.2 -> 5.2), then about 512 bytes
-// per lane.  In a batch the same choice measured slower (its series share the work
-// space by a per-bin cost that grows with the lanes per bin), so batches keep
-// stream_group.
+// per lane.  In a batch the same choice measured slower (3.8 -> 4.9 ms on the
+// 4096-series mix, also with the work space charged as for stream_group), so batches
+// keep stream_group.
 __host__ __device__ inline int stream_group_single(int64_t N, int64_t B, int elem_bytes) {
   const int64_t per_bin_bytes = (B > 0 ? N / B : N) * elem_bytes;
   if (per_bin_bytes <= 128) return 1;
