@@ -23,7 +23,10 @@ __global__ void __launch_bounds__(kBinsPerCta) k_bins(const __grid_constant__ Ba
   pdl_wait();
   pdl_trigger();
   const int64_t c = blockIdx.x;
-  if (threadIdx.x == 0) s_series = bt.cta_offs ? upper_index(bt.cta_offs, bt.n_series, c) : 0;
+  if (threadIdx.x < 32) {  // the CTA's series: a 32-ary warp search (3 rounds for 4096 series)
+    const int s = bt.cta_offs ? warp_upper_index(bt.cta_offs, bt.n_series, c, threadIdx.x) : 0;
+    if (threadIdx.x == 0) s_series = s;
+  }
   __syncthreads();
   const SeriesPlan& sp = plan_of(bt, s_series);
   const int64_t b = (c - sp.bincta_off) * kBinsPerCta + threadIdx.x;
